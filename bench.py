@@ -1,0 +1,376 @@
+"""Benchmark: merge evaluations/s of batched uneven merge scoring on GB300.
+
+Workload (one step = one pass of the whole hot path over one batch): 64
+cluster states (m = 2048, rank r = 64, each built from 8 appends, not timed)
+and 4096 candidate blocks of widths uniform in [16, 512]; every candidate is
+scored against its state: projection, Gram / residual, core spectrum,
+truncation, tail estimate and accept flag (Alg. 3 step 3).  Inputs (8.9 GB)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+Reported: device-resident throughput (``value``), the same through the
+public API with host<->device copies (``e2e``), the plain FP32 form of the
+same evaluations, the dominant kernel's roofline from CUDA events recorded
+around its launches, SM clocks sampled during the timed region, and the
+FP64 oracle on a bounded sample on the host cores (``cpu_baseline``).
+
+``--impl reference`` times the oracle alone on the same workload (a bounded
+sample per step) and prints its own line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "merge evaluations/s (incremental rank-r SVD) vs plain FP32 at <=1e-4 rel err"
+UNIT = "merge evals/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _work_per_candidate(m, rt, k):
+    """Algorithmic work of one mixed-form merge evaluation."""
+    n = rt + k
+    return dict(
+        gram_flops=2.0 * m * rt * k + 1.0 * m * k * (k + 1),
+        gram_bytes=4.0 * m * k + 4.0 * m * rt,
+        core_flops=(4.0 / 3.0) * n ** 3,
+    )
+
+
+def cpu_baseline(w, eps, budget_s=15.0, max_evals=64):
+    """Oracle (FP64 numpy) merge evaluations on a bounded sample of the same
+    workload: the states of the first candidates are rebuilt on the CPU
+    (untimed), then evaluations are timed until the budget is spent."""
+    import torch
+    from oracle import incremental as oinc
+
+    m, r = w["m"], w["r"]
+    need = sorted(set(w["cand_state"][:max_evals]))
+    states = {}
+    for s in need[:2]:
+        st = oinc.IncrementalSVD(m, r)
+        for b in w["states"][s]:
+            st.append(b.cpu())
+        states[s] = st
+    idx = [i for i in range(min(max_evals, len(w["candidates"]))) if w["cand_state"][i] in states]
+    blocks = {i: w["candidates"][i].cpu().double().numpy() for i in idx}
+    t0 = time.perf_counter()
+    done = 0
+    for i in idx:
+        states[w["cand_state"][i]].evaluate(blocks[i], eps)
+        done += 1
+        if time.perf_counter() - t0 > budget_s and done >= 4:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((p.get("num_threads", 1) for p in threadpool_info()), default=os.cpu_count())
+    except Exception:
+        cores = os.cpu_count()
+    ks = [w["candidates"][i].shape[1] for i in idx[:done]]
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} merge evaluations (m=2048, r={r}, k in {min(ks)}..{max(ks)}) "
+                      f"against 2 rebuilt states, FP64 numpy, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed as it stands on the host cores, same workload."""
+    import torch
+    from paper_2601_11626_gb300 import synth
+    from oracle import incremental as oinc
+
+    w = synth.scoring_c4(r=args.r, n_states=args.n_states, per_state=args.per_state, device="cpu")
+    m, r, eps = w["m"], w["r"], w["eps"]
+    st = oinc.IncrementalSVD(m, r)
+    for b in w["states"][0]:
+        st.append(b)
+    cands = [i for i in range(len(w["candidates"])) if w["cand_state"][i] == 0]
+    blocks = [w["candidates"][i].double().numpy() for i in cands]
+    per_step = max(1, args.ref_sample)
+    k = 0
+    for _ in range(args.warmup):
+        st.evaluate(blocks[k % len(blocks)], eps)
+        k += 1
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            st.evaluate(blocks[k % len(blocks)], eps)
+            k += 1
+            n += 1
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched uneven merge scoring (oracle sample)", "m": m, "r": r,
+                       "k_range": [16, 512], "sample_per_step": per_step},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": v, "unit": UNIT,
+                             "sample": f"{per_step} evaluations per step against one state"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--r", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--n-states", type=int, default=64)
+    ap.add_argument("--per-state", type=int, default=64)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-sample", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_11626_gb300 import csvd, synth
+
+    dev = torch.cuda.current_device()
+    w = synth.scoring_c4(r=args.r, seed=rank, n_states=args.n_states, per_state=args.per_state,
+                         device="cuda")
+    m, r, eps = w["m"], w["r"], w["eps"]
+    states = []
+    for blocks in w["states"]:
+        st = csvd.IncrSVD(m, r)
+        for b in blocks:
+            st.append(b)
+        states.append(st)
+    torch.cuda.synchronize()
+    ranks = [s.rank for s in states]
+    cands = w["candidates"]
+    n = len(cands)
+    batch = csvd.ScoreBatch(states, w["cand_state"], cands, eps, args.precision)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        batch.run()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        csvd.profile(True)
+        l0 = csvd.launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.run()
+        e1.record(stream)
+        e1.synchronize()
+        launches = csvd.launch_count() - l0
+        prof = csvd.profile_report()
+        csvd.profile(False)
+    ms = e0.elapsed_time(e1)
+    barrier()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    value = world * n * args.steps / (ms / 1000.0)
+
+    # dominant kernel roofline
+    peaks, peak_src = _peaks()
+    work = [_work_per_candidate(m, ranks[w["cand_state"][i]], cands[i].shape[1]) for i in range(n)]
+    gram_flops = sum(x["gram_flops"] for x in work)
+    gram_bytes = sum(x["gram_bytes"] for x in work)
+    core_flops = sum(x["core_flops"] for x in work)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tms) = top
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if name.startswith("core"):
+        achieved = core_flops * args.steps / (tms / 1000.0) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    else:
+        achieved = gram_bytes * args.steps / (tms / 1000.0) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_note": f"{peak_src} copy bandwidth"}
+    roof["kernels"] = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(x[1] for x in prof.values())}
+                       for k, v in prof.items()}
+
+    # plain FP32 form of the same evaluations
+    plain = None
+    if args.plain_steps > 0 and args.precision == "mixed":
+        pb = csvd.ScoreBatch(states, w["cand_state"], cands, eps, "plain")
+        pb.run()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            pb.run()
+        p1.record(stream)
+        p1.synchronize()
+        pms = p0.elapsed_time(p1) / args.plain_steps
+        plain = {"value": world * n / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "steps": args.plain_steps,
+                 "max_tail_rel_diff_vs_mixed": float(((pb.tail.sqrt() - batch.tail.sqrt()).abs()
+                                                      / batch.tail.sqrt().clamp_min(1e-300)).max()),
+                 "accept_agree": bool((pb.accept == batch.accept).all())}
+        del pb
+
+    # end to end through the public API: inputs from pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        pool = w["pools"][1]
+        host = torch.empty(pool.shape, dtype=pool.dtype, pin_memory=True)
+        host.copy_(pool)
+        out_bytes = batch.tail.numel() * 8 + batch.accept.numel() + batch.sigma.numel() * 4
+        o_tail = torch.empty(batch.tail.shape, dtype=batch.tail.dtype, pin_memory=True)
+        o_acc = torch.empty(batch.accept.shape, dtype=batch.accept.dtype, pin_memory=True)
+        o_sig = torch.empty(batch.sigma.shape, dtype=batch.sigma.dtype, pin_memory=True)
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.e2e_steps):
+            pool.copy_(host, non_blocking=True)
+            batch.run()
+            o_tail.copy_(batch.tail, non_blocking=True)
+            o_acc.copy_(batch.accept, non_blocking=True)
+            o_sig.copy_(batch.sigma, non_blocking=True)
+        q1.record(stream)
+        q1.synchronize()
+        qms = q0.elapsed_time(q1) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([qms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            qms = float(t)
+        e2e = {"value": world * n / (qms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": pool.numel() * pool.element_size(),
+               "d2h_bytes_per_step": out_bytes, "ms_per_step": qms, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, eps)
+
+    if rank == 0:
+        ks = [c.shape[1] for c in cands]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"batched uneven merge scoring: {len(states)} states x {args.per_state} "
+                            f"candidates per GPU, m={m}, k~U[16,512], r={r}",
+                "m": m, "r": r, "n_candidates": n, "k_mean": sum(ks) / n, "k_range": [16, 512],
+                "precision_form": args.precision, "eps": eps,
+                "l2": "inputs (%.1f GB) larger than L2, no flush" % (
+                    w["pools"][1].numel() * 4 / 1e9),
+                "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
+            "plain_fp32": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    for st in states:
+        st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * csvd -- incremental truncated SVD of horizontally concatenated matrices,
+ * its tail-error estimate and bounds, and error-constrained clustering, on
+ * one NVIDIA GB300 GPU (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * Method: arXiv 2601.11626, "Concatenated Matrix SVD: Compression Bounds,
+ * Incremental Approximation, and Error-Constrained Clustering".
+ *
+ * Conventions (all entry points):
+ *   - A block A_j is row-major m x k: element (i, c) at ptr[i * ld + c],
+ *     ld >= k, in DEVICE memory, dtype CSVD_F32 or CSVD_BF16.  Block memory is
+ *     borrowed: it must stay valid until the work enqueued on the stream has
+ *     finished.  A 16-byte-aligned ptr with ld a multiple of 8 (f32) or 16
+ *     (bf16) lets the batched scorer stage tiles with bulk (TMA) copies;
+ *     other layouts take a register-load path.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream).  Calls documented as "syncs" wait
+ *     for that stream before returning host values.
+ *   - Errors are returned as csvd_status; no exception crosses the ABI.
+ *     csvd_last_error() gives a thread-local message for the last failure.
+ *     Device-side conditions (an iteration cap reached) set a status word that
+ *     the next synchronising call returns.
+ *   - State objects own their device memory.  Temporary workspace comes from
+ *     the allocator installed with csvd_set_allocator (default: the CUDA
+ *     stream-ordered pool, cudaMallocAsync / cudaFreeAsync).
+ *
+ * Notation (paper -> here): Q_t -> U (m x r_t, orthonormal), S_t = diag(s^2)
+ * -> sigma (r_t values), Y = Q_t^T A -> P, residual R = A - Q_t Y, thin QR
+ * R = Q_res B, core K = [[diag(sigma), P], [0, B]] (K K^T = S_{t+1}).
+ */
+#ifndef CSVD_H_
+#define CSVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CSVD_OK = 0,
+  CSVD_ERR_ARG = 1,            /* invalid argument (NULL, negative size, bad enum) */
+  CSVD_ERR_SHAPE = 2,          /* block row count differs from the state's m, or a size limit */
+  CSVD_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  CSVD_ERR_OOM = 4,            /* device allocation failed */
+  CSVD_ERR_NOT_CONVERGED = 5,  /* an iterative core solver hit its sweep cap */
+  CSVD_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  CSVD_ERR_UNIMPLEMENTED = 7
+} csvd_status;
+
+typedef enum { CSVD_F32 = 0, CSVD_BF16 = 1 } csvd_dtype;
+
+/* Arithmetic of the merge evaluation:
+ *   CSVD_PLAIN_FP32 -- the step as the Lemma states it, all in FP32 SIMT:
+ *     P = U^T A, R = A - U P with one re-orthogonalisation pass, Householder
+ *     QR of R, one-sided Jacobi SVD of the core K.
+ *   CSVD_MIXED -- the same quantities from one pass over A on the tensor
+ *     cores: P = U^T A and A^T A (bf16 split operands, FP32 accumulation), the
+ *     core's eigenvalues from the Gram K^T K = [[S, diag(s) P],[P^T diag(s),
+ *     A^T A]] by Householder tridiagonalisation and bisection; tails in FP64. */
+typedef enum { CSVD_PLAIN_FP32 = 0, CSVD_MIXED = 1 } csvd_precision;
+
+typedef enum { CSVD_ALG_WEYL = 1, CSVD_ALG_RESIDUAL = 2, CSVD_ALG_APPROX = 3 } csvd_algo;
+typedef enum { CSVD_SORT_FROBENIUS = 0, CSVD_SORT_RESIDUAL = 1 } csvd_sort;
+
+typedef struct {
+  const void* ptr;  /* device pointer to element (0, 0) */
+  int64_t k;        /* columns (block width n_i), 1 <= k */
+  int64_t ld;       /* row pitch in elements, ld >= k */
+  int32_t dtype;    /* csvd_dtype */
+  int32_t reserved; /* must be 0 */
+} csvd_block;
+
+typedef struct csvd_state_s* csvd_state;
+
+typedef void* (*csvd_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*csvd_free_fn)(void* ptr, void* stream, void* ctx);
+
+/* Install a device allocator for temporary workspace (e.g. a framework's
+ * caching allocator); NULL, NULL restores the default stream-ordered pool.
+ * Process-wide; not thread-safe against concurrent csvd calls. */
+csvd_status csvd_set_allocator(csvd_alloc_fn alloc, csvd_free_fn free_, void* ctx);
+
+/* Create an empty rank-r state for blocks with m rows (M_0 := 0, Thm. 2's
+ * convention; Lemma 1 applied from the empty state gives the rank-r SVD of
+ * the first block, Alg. 3 step 1).  1 <= r <= m <= 65536, r <= 1024.
+ * The state owns U (m x r), sigma (r) and FP64 scalars on the device. */
+csvd_status csvd_incr_init(csvd_state* out, int64_t m, int32_t r, int32_t precision,
+                           void* cuda_stream);
+
+/* Append one block (Lemma 1 + Cor. 3, Appendix B): projection, residual,
+ * thin QR, core SVD, truncation back to rank min(r, r_t + k', m) with
+ * k' = min(k, m - r_t), and the energy update sum_i ||A_i||_F^2.
+ * Stream-ordered, asynchronous.  A->ptr must hold m rows. */
+csvd_status csvd_incr_append(csvd_state s, const csvd_block* A);
+
+/* Copy the retained singular values sigma~_1..r_eff (Cor. 3, item 2) to
+ * host memory (at least r floats) and the current rank.  Syncs. */
+csvd_status csvd_incr_sigma(csvd_state s, float* sigma_host, int32_t* r_eff);
+
+/* Copy the current basis U (m x r_eff, row-major, leading dimension ldu)
+ * into a caller-owned device buffer.  Stream-ordered. */
+csvd_status csvd_incr_basis(csvd_state s, float* U_dev, int64_t ldu);
+
+/* Plug-in estimate of Cor. 2, E~_r^2 = sum_i ||A_i||_F^2 - sum_{j<=r}
+ * sigma~_j^2, and E~_r / ||M||_F.  tail_sq is the accumulated discarded
+ * energy (equal in exact arithmetic, free of the subtraction's
+ * cancellation); tail_sq_paper, if non-NULL, is the subtraction evaluated
+ * in FP64; energy, if non-NULL, is ||M||_F^2.  Syncs. */
+csvd_status csvd_tail_error(csvd_state s, double* tail_sq, double* tail_rel,
+                            double* tail_sq_paper, double* energy);
+
+/* Release the state.  Syncs its stream first. */
+csvd_status csvd_incr_free(csvd_state s);
+
+/* Batched merge evaluation (Alg. 3 step 3(a)-(e)): for every candidate i,
+ * a tentative append of cands[i] to states[cand_state[i]] producing
+ * sigma~ (first r_i = rank after the append values, row i of sigma_out with
+ * leading dimension ld_sigma), E~^2 (tail_sq_out[i]) and the accept flag
+ * accept_out[i] = (E~^2 <= eps^2 * (||M_C||^2 + ||A_i||^2)).  No state is
+ * modified.  Outputs are DEVICE pointers (tail_paper_out may be NULL).
+ * All states must share m and the stream of states[0] is used.
+ * precision selects CSVD_PLAIN_FP32 or CSVD_MIXED. */
+csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
+                       const csvd_block* cands, int32_t n, double eps, int32_t precision,
+                       float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                       double* tail_paper_out, uint8_t* accept_out);
+
+/* Bounds for blocks taken in the given order (Section 3):
+ *   weyl_sq     Thm. 1: sum ||A_j||^2 - max_j sum_{i<=r} sigma_i^2(A_j)
+ *   residual_sq Cor. 1: sum ||A_j||^2 - sum_{j<=r} mu_j^2, mu the singular
+ *               values of the residuals against a full-span basis
+ *   plugin_sq   Cor. 2 with a rank-r incremental state
+ *   energy      sum ||A_j||^2
+ * Host outputs (any may be NULL).  Syncs. */
+csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
+                        void* cuda_stream, double* weyl_sq, double* residual_sq,
+                        double* plugin_sq, double* energy);
+
+/* Error-constrained clustering, Algorithms 1-3 of Appendix E.  labels_out[j]
+ * receives the cluster index of block j (clusters numbered in creation
+ * order); cluster_est_sq_out (length n, may be NULL) receives each cluster's
+ * certificate value (bound^2 or E~^2) at its index; energy_out likewise
+ * ||M_C||^2; compression_ratio_out (may be NULL) the ratio of stored numbers
+ * (Section 4).  Host outputs.  Syncs. */
+csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t m, int32_t r, double eps,
+                         int32_t algo, int32_t sort_mode, int32_t precision, void* cuda_stream,
+                         int32_t* labels_out, double* cluster_est_sq_out, double* energy_out,
+                         double* compression_ratio_out);
+
+/* Backward of E = sum_j ||(I - U U^T) A_j||_F^2 for a fixed basis U (m x r,
+ * row-major, device, leading dimension ldu): dA_j = 2 g (I - U U^T) A_j
+ * written to grads[j] (f32 blocks with their own ld).  With U the top-r left
+ * singular vectors of the concatenation this is the gradient of the
+ * Eckart-Young tail (Thm. 4), valid when sigma_r > sigma_{r+1}.
+ * Stream-ordered. */
+csvd_status csvd_tail_grad(const float* U, int64_t ldu, int64_t m, int32_t r,
+                           const csvd_block* blocks, const csvd_block* grads, int32_t n,
+                           double g, void* cuda_stream);
+
+/* ||A_j||_F^2 of each block (Kahan-compensated FP32 partial sums, FP64
+ * totals) into energy_host[0..n).  Syncs. */
+csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m, void* cuda_stream,
+                              double* energy_host);
+
+/* Launch tracing.  csvd_launch_count: kernels launched by this library so
+ * far in the process.  csvd_profile(1) clears and starts recording a pair of
+ * CUDA events on the launch stream around every kernel launch, csvd_profile(0)
+ * clears and stops; csvd_profile_report writes one line per kernel name,
+ * "name launches total_ms", into buf (NUL-terminated, truncated to len) and
+ * waits for the recorded events. */
+int64_t csvd_launch_count(void);
+csvd_status csvd_profile(int32_t enable);
+csvd_status csvd_profile_report(char* buf, int64_t len);
+
+/* Thread-local message describing the last non-OK status (never NULL). */
+const char* csvd_last_error(void);
+
+/* Library version string. */
+const char* csvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSVD_H_ */

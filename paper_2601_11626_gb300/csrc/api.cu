@@ -1,0 +1,1378 @@
+// Host side of the csvd C ABI: state objects, workspace, batched pipelines
+// for the merge evaluation (plain and mixed forms), the basis commit, the
+// bounds, the clustering drivers of Algorithms 1-3 and the tail gradient.
+//
+// Every pipeline is a fixed sequence of batched launches; the host only
+// builds descriptor tables (uploaded once per call through a pinned staging
+// ring) and, in the clustering drivers, takes the greedy decisions between
+// launches.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "csvd.h"
+#include "common.cuh"
+
+using namespace csvd;
+
+// =================================================================== errors
+static thread_local std::string g_err = "";
+
+static csvd_status fail(csvd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? CSVD_ERR_OOM : CSVD_ERR_CUDA,      \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+#define CSVD_TRY(expr)                    \
+  do {                                    \
+    csvd_status s_ = (expr);              \
+    if (s_ != CSVD_OK) return s_;         \
+  } while (0)
+
+// ================================================================ tracing
+namespace csvd {
+static std::atomic<long long> g_launch_count{0};
+static std::atomic<bool> g_prof_on{false};
+struct ProfEv {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::vector<ProfEv> g_prof;
+static thread_local cudaEvent_t t_prof_begin = nullptr;
+
+void prof_begin(cudaStream_t s) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  if (cudaEventCreate(&t_prof_begin) != cudaSuccess) { t_prof_begin = nullptr; return; }
+  cudaEventRecord(t_prof_begin, s);
+}
+
+void prof_end(const char* name, cudaStream_t s) {
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof_on.load(std::memory_order_relaxed) || !t_prof_begin) return;
+  cudaEvent_t b = nullptr;
+  if (cudaEventCreate(&b) != cudaSuccess) return;
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(ProfEv{name, t_prof_begin, b});
+  t_prof_begin = nullptr;
+}
+}  // namespace csvd
+
+// =============================================================== allocation
+static csvd_alloc_fn g_alloc = nullptr;
+static csvd_free_fn g_free = nullptr;
+static void* g_actx = nullptr;
+static std::once_flag g_pool_once;
+
+static void* dev_alloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 256;
+  if (g_alloc) return g_alloc(bytes, (void*)s, g_actx);
+  std::call_once(g_pool_once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+    }
+  });
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+  return p;
+}
+
+static void dev_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) g_free(p, (void*)s, g_actx);
+  else cudaFreeAsync(p, s);
+}
+
+// Byte layout of one workspace allocation (256-byte aligned pieces).
+struct Layout {
+  size_t size = 0;
+  size_t add(size_t bytes) {
+    size_t off = (size + 255) & ~size_t(255);
+    size = off + bytes;
+    return off;
+  }
+};
+
+struct Workspace {
+  char* base = nullptr;
+  cudaStream_t s = nullptr;
+  ~Workspace() { dev_free(base, s); }
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+// Pinned host staging ring for descriptor uploads.
+struct StagingRing {
+  struct Slot {
+    void* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+  };
+  static constexpr int kSlots = 16;
+  std::mutex mu;
+  Slot slots[kSlots];
+  int next = 0;
+};
+static StagingRing g_ring;
+
+static cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_ring.mu);
+  StagingRing::Slot& sl = g_ring.slots[g_ring.next];
+  g_ring.next = (g_ring.next + 1) % StagingRing::kSlots;
+  cudaError_t e;
+  if (sl.used) {
+    e = cudaEventSynchronize(sl.ev);
+    if (e != cudaSuccess) return e;
+  }
+  if (sl.cap < bytes) {
+    if (sl.host) cudaFreeHost(sl.host);
+    sl.host = nullptr;
+    size_t cap = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+    e = cudaHostAlloc(&sl.host, cap, cudaHostAllocPortable);
+    if (e != cudaSuccess) { sl.cap = 0; return e; }
+    sl.cap = cap;
+  }
+  if (!sl.ev) {
+    e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  std::memcpy(sl.host, src, bytes);
+  e = cudaMemcpyAsync(dst, sl.host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(sl.ev, s);
+  sl.used = true;
+  return e;
+}
+
+// Host-side packing of descriptor tables into one upload.
+struct Pack {
+  std::vector<char> buf;
+  template <class T>
+  size_t add(const std::vector<T>& v) {
+    size_t off = (buf.size() + 255) & ~size_t(255);
+    buf.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+// ============================================================ GEMM batches
+struct GemmBatch {
+  std::vector<GemmDesc> descs;
+  std::vector<GemmTile> tiles;
+  size_t off_d = 0, off_t = 0;
+  void add(const GemmDesc& d, bool upper_only = false) {
+    if (d.M <= 0 || d.N <= 0) return;
+    const int id = (int)descs.size();
+    descs.push_back(d);
+    const int tm = (d.M + kGemmBM - 1) / kGemmBM, tn = (d.N + kGemmBN - 1) / kGemmBN;
+    for (int a = 0; a < tm; ++a)
+      for (int b = 0; b < tn; ++b)
+        if (!upper_only || a <= b) tiles.push_back(GemmTile{id, a, b, 0});
+  }
+  void pack(Pack& p) {
+    off_d = p.add(descs);
+    off_t = p.add(tiles);
+  }
+  cudaError_t launch(char* dbase, cudaStream_t s) const {
+    if (tiles.empty()) return cudaSuccess;
+    return launch_gemm(reinterpret_cast<const GemmDesc*>(dbase + off_d),
+                       reinterpret_cast<const GemmTile*>(dbase + off_t), (int)tiles.size(), s);
+  }
+};
+
+static GemmDesc gemm(const void* A, int64_t lda, int tA, const void* B, int64_t ldb, int tB,
+                     float* C, int64_t ldc, int tC, int M, int N, int K, float alpha = 1.f,
+                     const float* Cin = nullptr, int64_t ldcin = 0, int tCin = 0,
+                     float beta = 0.f, int a_bf16 = 0, int b_bf16 = 0) {
+  GemmDesc d;
+  d.A = A; d.B = B; d.Cin = Cin; d.C = C;
+  d.lda = lda; d.ldb = ldb; d.ldcin = ldcin; d.ldc = ldc;
+  d.M = M; d.N = N; d.K = K;
+  d.tA = tA; d.tB = tB; d.tCin = tCin; d.tC = tC;
+  d.a_bf16 = a_bf16; d.b_bf16 = b_bf16;
+  d.alpha = alpha; d.beta = beta;
+  return d;
+}
+
+// ================================================================== state
+struct csvd_state_s {
+  int64_t m = 0;
+  int r = 0;
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  int rt = 0;
+  int nblocks = 0;
+  float* U[2] = {nullptr, nullptr};  // m x r row-major (ld r), double-buffered
+  int cur = 0;
+  float* sigma = nullptr;  // r
+  double* scal = nullptr;  // {energy, discarded}
+  int* status = nullptr;   // device status word
+};
+
+// Read-only view of a state for the batched pipelines.
+struct StateView {
+  const float* U;
+  int64_t ldu;
+  int rt, r;
+  const float* sigma;
+  const double* scal;
+};
+
+static StateView view_of(const csvd_state_s* s) {
+  return StateView{s->U[s->cur], s->r, s->rt, s->r, s->sigma, s->scal};
+}
+
+static csvd_status check_block(const csvd_block* b, int64_t m) {
+  if (!b || !b->ptr) return fail(CSVD_ERR_ARG, "block pointer is NULL");
+  if (b->k < 1 || b->ld < b->k) return fail(CSVD_ERR_ARG, "block needs k >= 1 and ld >= k");
+  if (b->dtype != CSVD_F32 && b->dtype != CSVD_BF16) return fail(CSVD_ERR_ARG, "bad dtype");
+  if (b->k > (int64_t)1 << 20) return fail(CSVD_ERR_SHAPE, "block too wide");
+  (void)m;
+  return CSVD_OK;
+}
+
+static csvd_status take_status(int* d_status, cudaStream_t s) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+    if (h & kStatusJacobiCap) return fail(CSVD_ERR_NOT_CONVERGED, "Jacobi core hit its sweep cap");
+    if (h & kStatusBisectCap) return fail(CSVD_ERR_NOT_CONVERGED, "bisection hit its iteration cap");
+    if (h & kStatusWaitCap) return fail(CSVD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return fail(CSVD_ERR_SHAPE, "device kernel reported bad sizes");
+  }
+  return CSVD_OK;
+}
+
+// Largest core kept in shared memory (bytes of dynamic shared memory).
+static constexpr int kCoreSmemBudget = 200 * 1024;
+
+// ===================================================== the batched pipeline
+// One merge evaluation per item: (state view, block).  Produces sigma~,
+// tails, energies and accept flags into caller arrays (device).  When
+// `want_W` is set (plain form only) the left vectors Wt and the QR
+// workspace stay alive in `keep` for a basis commit.
+struct Item {
+  StateView st;
+  const csvd_block* blk;
+  int r;        // target rank
+  int64_t m;
+  // outputs (device)
+  float* sigma_out;
+  double* tail_out;
+  double* tail_paper_out;
+  double* energy_out;
+  uint8_t* accept_out;
+};
+
+struct CommitKeep {  // workspace kept for the commit of a single plain item
+  float* Rt = nullptr;
+  float* tau = nullptr;
+  float* Wt = nullptr;
+  int kp = 0, nr = 0, r_new = 0;
+};
+
+static csvd_status run_items(const std::vector<Item>& items, double eps, int precision,
+                             cudaStream_t s, int* d_status, Workspace& ws, CommitKeep* keep,
+                             bool want_W) {
+  const int n = (int)items.size();
+  if (n == 0) return CSVD_OK;
+  Layout L;
+  struct Off { size_t energy, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new; bool smem; };
+  std::vector<Off> off(n);
+  const bool mixed = (precision == CSVD_MIXED) && !want_W;
+  for (int i = 0; i < n; ++i) {
+    const Item& it = items[i];
+    const int64_t m = it.m;
+    const int k = (int)it.blk->k, rt = it.st.rt;
+    Off& o = off[i];
+    o.kp = (int)std::min<int64_t>(k, m - rt);
+    o.nr = rt + o.kp;
+    o.nc = rt + k;
+    o.r_new = std::min(it.r, o.nr);
+    o.energy = L.add(sizeof(double));
+    o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
+    if (mixed) {
+      o.G = L.add(sizeof(float) * (size_t)k * k);
+      const int nn = rt + k;
+      const int need = (tridiag_scratch_floats(nn) + nn * nn) * 4;
+      o.smem = need <= kCoreSmemBudget;
+      o.ldwork = nn;
+      o.work = o.smem ? 0 : L.add(sizeof(float) * (size_t)nn * nn);
+    } else {
+      o.P2 = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
+      o.Rt = L.add(sizeof(float) * (size_t)k * m);
+      o.tau = L.add(sizeof(float) * (size_t)std::max(o.kp, 1));
+      o.B = L.add(sizeof(float) * (size_t)std::max(o.kp, 1) * k);
+      const int ncp = o.nc + (o.nc & 1);
+      const int need = (jacobi_scratch_floats(o.nc) + ncp * o.nr) * 4;
+      o.smem = need <= kCoreSmemBudget;
+      o.ldwork = o.nr;
+      o.work = o.smem ? 0 : L.add(sizeof(float) * (size_t)ncp * o.nr);
+      o.Wt = want_W ? L.add(sizeof(float) * (size_t)std::max(o.r_new, 1) * o.nr) : 0;
+    }
+  }
+  // descriptor tables are filled after allocation (they hold device pointers)
+  const size_t energy_lo = off[0].energy;
+  (void)energy_lo;
+  // upper bound for the descriptor region: computed after building with a dummy base
+  // -> build twice: sizes do not depend on the base pointer.
+  auto build = [&](char* base, Pack& pk, GemmBatch& gP, GemmBatch& gR, GemmBatch& gP2,
+                   GemmBatch& gRu, GemmBatch& gG, std::vector<EnergyDesc>& ed,
+                   std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
+                   std::vector<CoreDesc>& cd_g) {
+    int max_m = 1;
+    for (int i = 0; i < n; ++i) {
+      const Item& it = items[i];
+      const Off& o = off[i];
+      const int64_t m = it.m;
+      const int k = (int)it.blk->k, rt = it.st.rt;
+      const int bf = it.blk->dtype == CSVD_BF16;
+      max_m = std::max<int>(max_m, (int)m);
+      double* energy = reinterpret_cast<double*>(base + o.energy);
+      float* P = rt > 0 ? reinterpret_cast<float*>(base + o.P) : nullptr;
+      EnergyDesc e{it.blk->ptr, it.blk->ld, (int)m, k, bf, 0, energy};
+      ed.push_back(e);
+      if (rt > 0)
+        gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, k, 0, rt, k, (int)m,
+                    1.f, nullptr, 0, 0, 0.f, 0, bf));
+      CoreDesc c;
+      std::memset(&c, 0, sizeof(c));
+      c.P = P;
+      c.P2 = nullptr;
+      c.ldp = k;
+      c.sigma = it.st.sigma;
+      c.scal = it.st.scal;
+      c.energy_add = energy;
+      c.sigma_out = it.sigma_out;
+      c.tail_out = it.tail_out;
+      c.tail_paper_out = it.tail_paper_out;
+      c.energy_out = it.energy_out;
+      c.accept_out = it.accept_out;
+      c.eps = eps;
+      c.rt = rt;
+      c.k = k;
+      c.kp = o.kp;
+      c.r_new = o.r_new;
+      c.in_smem = o.smem ? 1 : 0;
+      c.work = o.smem ? nullptr : reinterpret_cast<float*>(base + o.work);
+      c.ldwork = o.ldwork;
+      if (mixed) {
+        float* G = reinterpret_cast<float*>(base + o.G);
+        gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, k, 0, k, k,
+                    (int)m, 1.f, nullptr, 0, 0, 0.f, bf, bf), true);
+        c.Gaa = G;
+        c.ldb = k;
+      } else {
+        if (bf) return false;
+        float* P2 = rt > 0 ? reinterpret_cast<float*>(base + o.P2) : nullptr;
+        float* Rt = reinterpret_cast<float*>(base + o.Rt);
+        // R^T = (A - U P)^T  (K = 0 when rt == 0: a transpose copy)
+        gR.add(gemm(it.st.U, it.st.ldu, 0, P, k, 0, Rt, m, 1, (int)m, k, rt, -1.f,
+                    reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, 0, 1.f));
+        if (rt > 0) {
+          gP2.add(gemm(it.st.U, it.st.ldu, 1, Rt, m, 1, P2, k, 0, rt, k, (int)m));
+          gRu.add(gemm(it.st.U, it.st.ldu, 0, P2, k, 0, Rt, m, 1, (int)m, k, rt, -1.f, Rt, m,
+                       1, 1.f));
+        }
+        QRDesc q{Rt, m, reinterpret_cast<float*>(base + o.tau), reinterpret_cast<float*>(base + o.B),
+                 k, (int)m, k, o.kp, 0};
+        if (o.kp > 0) qd.push_back(q);
+        c.P2 = P2;
+        c.B = reinterpret_cast<float*>(base + o.B);
+        c.ldb = k;
+        if (want_W) {
+          c.Wt = reinterpret_cast<float*>(base + o.Wt);
+          c.ldw = o.nr;
+        }
+      }
+      (o.smem ? cd_s : cd_g).push_back(c);
+    }
+    gP.pack(pk); gR.pack(pk); gP2.pack(pk); gRu.pack(pk); gG.pack(pk);
+    (void)max_m;
+    return true;
+  };
+  // pass 1: sizes of the descriptor region
+  size_t desc_bytes = 0;
+  {
+    Pack pk;
+    GemmBatch a, b, c, d, e;
+    std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg;
+    char* fake = reinterpret_cast<char*>(uintptr_t(1) << 20);
+    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg))
+      return fail(CSVD_ERR_UNIMPLEMENTED, "bf16 blocks need the mixed form");
+    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg);
+    desc_bytes = pk.buf.size();
+  }
+  const size_t off_desc = L.add(desc_bytes);
+  ws.s = s;
+  ws.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!ws.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  Pack pk;
+  GemmBatch gP, gR, gP2, gRu, gG;
+  std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g;
+  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g);
+  const size_t o_ed = pk.add(ed), o_qd = pk.add(qd), o_cs = pk.add(cd_s), o_cg = pk.add(cd_g);
+  char* dbase = ws.base + off_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  // energies start at zero
+  for (int i = 0; i < n; ++i) CUDA_TRY(cudaMemsetAsync(ws.base + off[i].energy, 0, 8, s));
+  int max_chunks = 1;
+  int max_m = 1;
+  for (int i = 0; i < n; ++i) {
+    const int64_t tot = items[i].m * items[i].blk->k;
+    max_chunks = std::max<int>(max_chunks, (int)std::min<int64_t>(64, (tot + 8191) / 8192));
+    max_m = std::max<int>(max_m, (int)items[i].m);
+  }
+  CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
+  CUDA_TRY(gP.launch(dbase, s));
+  if (mixed) {
+    CUDA_TRY(gG.launch(dbase, s));
+    int sm = 0;
+    for (auto& c : cd_s) sm = std::max(sm, (tridiag_scratch_floats(c.rt + c.k) + (c.rt + c.k) * (c.rt + c.k)) * 4);
+    int gm = 0;
+    for (auto& c : cd_g) gm = std::max(gm, tridiag_scratch_floats(c.rt + c.k) * 4);
+    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(), sm, d_status, s));
+    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(), gm, d_status, s));
+  } else {
+    CUDA_TRY(gR.launch(dbase, s));
+    CUDA_TRY(gP2.launch(dbase, s));
+    CUDA_TRY(gRu.launch(dbase, s));
+    CUDA_TRY(launch_householder_qr(reinterpret_cast<QRDesc*>(dbase + o_qd), (int)qd.size(), max_m, s));
+    int sm = 0;
+    for (auto& c : cd_s) {
+      const int nc = c.rt + c.k, nr = c.rt + c.kp;
+      sm = std::max(sm, (jacobi_scratch_floats(nc) + (nc + (nc & 1)) * nr) * 4);
+    }
+    int gm = 0;
+    for (auto& c : cd_g) gm = std::max(gm, jacobi_scratch_floats(c.rt + c.k) * 4);
+    CUDA_TRY(launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(), sm, d_status, s));
+    CUDA_TRY(launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(), gm, d_status, s));
+  }
+  if (keep && n == 1 && !mixed) {
+    keep->Rt = ws.at<float>(off[0].Rt);
+    keep->tau = ws.at<float>(off[0].tau);
+    keep->Wt = want_W ? ws.at<float>(off[0].Wt) : nullptr;
+    keep->kp = off[0].kp;
+    keep->nr = off[0].nr;
+    keep->r_new = off[0].r_new;
+  }
+  return CSVD_OK;
+}
+
+// Tentative append of one block and commit of the rotated basis (Cor. 3):
+// U_new = U W_top + Q_res W_bot.
+static csvd_status append_commit(csvd_state_s* st, const csvd_block* A) {
+  cudaStream_t s = st->stream;
+  const int k = (int)A->k;
+  const int kp = (int)std::min<int64_t>(k, st->m - st->rt);
+  const int r_new = std::min(st->r, st->rt + kp);
+  // small outputs of the evaluation
+  Layout L;
+  const size_t o_sig = L.add(sizeof(float) * std::max(r_new, 1));
+  const size_t o_tail = L.add(sizeof(double) * 3);
+  const size_t o_Zt = L.add(sizeof(float) * (size_t)std::max(r_new, 1) * st->m);
+  const size_t o_desc = L.add(4096);
+  Workspace w2;
+  w2.s = s;
+  w2.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w2.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  float* sig_new = w2.at<float>(o_sig);
+  double* tails = w2.at<double>(o_tail);
+  Item it{view_of(st), A, st->r, st->m, sig_new, tails + 1, nullptr, tails + 0, nullptr};
+  Workspace ws;
+  CommitKeep keep;
+  CSVD_TRY(run_items({it}, 0.0, CSVD_PLAIN_FP32, s, st->status, ws, &keep, true));
+  float* Zt = w2.at<float>(o_Zt);
+  Pack pk;
+  std::vector<ApplyQDesc> ad;
+  if (kp > 0 && r_new > 0) {
+    ad.push_back(ApplyQDesc{keep.Rt, st->m, keep.tau, keep.Wt, keep.nr, st->rt, Zt, st->m,
+                            (int)st->m, kp, r_new, 0});
+  } else {
+    CUDA_TRY(cudaMemsetAsync(Zt, 0, sizeof(float) * (size_t)std::max(r_new, 1) * st->m, s));
+  }
+  GemmBatch gU;
+  float* Unew = st->U[1 - st->cur];
+  gU.add(gemm(st->U[st->cur], st->r, 0, keep.Wt, keep.nr, 1, Unew, st->r, 0, (int)st->m, r_new,
+              st->rt, 1.f, Zt, st->m, 1, 1.f));
+  const size_t o_ad = pk.add(ad);
+  gU.pack(pk);
+  if (pk.buf.size() > 4096) return fail(CSVD_ERR_ARG, "internal: descriptor region too small");
+  char* dbase = w2.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  if (!ad.empty())
+    CUDA_TRY(launch_apply_q(reinterpret_cast<ApplyQDesc*>(dbase + o_ad), 1, r_new, s));
+  CUDA_TRY(gU.launch(dbase, s));
+  CUDA_TRY(launch_state_commit(sig_new, r_new, st->sigma, tails + 0, tails + 1, st->scal, s));
+  st->cur = 1 - st->cur;
+  st->rt = r_new;
+  st->nblocks += 1;
+  return CSVD_OK;
+}
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* csvd_last_error(void) { return g_err.c_str(); }
+const char* csvd_version(void) { return "csvd 0.1 (sm_103a)"; }
+
+csvd_status csvd_set_allocator(csvd_alloc_fn alloc, csvd_free_fn free_, void* ctx) {
+  if ((alloc == nullptr) != (free_ == nullptr))
+    return fail(CSVD_ERR_ARG, "allocator and free must both be set or both be NULL");
+  g_alloc = alloc;
+  g_free = free_;
+  g_actx = ctx;
+  return CSVD_OK;
+}
+
+csvd_status csvd_incr_init(csvd_state* out, int64_t m, int32_t r, int32_t precision,
+                           void* cuda_stream) {
+  if (!out) return fail(CSVD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || m > 65536 || r < 1 || r > 1024 || r > m)
+    return fail(CSVD_ERR_ARG, "need 1 <= r <= min(m, 1024), m <= 65536");
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+    return fail(CSVD_ERR_ARG, "bad precision");
+  csvd_state_s* st = new csvd_state_s();
+  st->m = m;
+  st->r = r;
+  st->prec = precision;
+  st->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&st->U[b], sizeof(float) * m * r);
+  if (e == cudaSuccess) e = cudaMalloc(&st->sigma, sizeof(float) * r);
+  if (e == cudaSuccess) e = cudaMalloc(&st->scal, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&st->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->scal, 0, sizeof(double) * 4, st->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->status, 0, sizeof(int), st->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->sigma, 0, sizeof(float) * r, st->stream);
+  if (e != cudaSuccess) {
+    csvd_incr_free(st);
+    return fail(e == cudaErrorMemoryAllocation ? CSVD_ERR_OOM : CSVD_ERR_CUDA,
+                std::string("state allocation: ") + cudaGetErrorString(e));
+  }
+  *out = st;
+  return CSVD_OK;
+}
+
+csvd_status csvd_incr_free(csvd_state st) {
+  if (!st) return CSVD_OK;
+  if (st->stream || st->U[0]) cudaStreamSynchronize(st->stream);
+  cudaFree(st->U[0]);
+  cudaFree(st->U[1]);
+  cudaFree(st->sigma);
+  cudaFree(st->scal);
+  cudaFree(st->status);
+  delete st;
+  return CSVD_OK;
+}
+
+csvd_status csvd_incr_append(csvd_state st, const csvd_block* A) {
+  if (!st) return fail(CSVD_ERR_ARG, "state is NULL");
+  CSVD_TRY(check_block(A, st->m));
+  if (A->dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "append takes f32 blocks");
+  return append_commit(st, A);
+}
+
+csvd_status csvd_incr_sigma(csvd_state st, float* sigma_host, int32_t* r_eff) {
+  if (!st) return fail(CSVD_ERR_ARG, "state is NULL");
+  if (r_eff) *r_eff = st->rt;
+  if (sigma_host && st->rt > 0)
+    CUDA_TRY(cudaMemcpyAsync(sigma_host, st->sigma, sizeof(float) * st->rt,
+                             cudaMemcpyDeviceToHost, st->stream));
+  return take_status(st->status, st->stream);
+}
+
+csvd_status csvd_incr_basis(csvd_state st, float* U_dev, int64_t ldu) {
+  if (!st || !U_dev) return fail(CSVD_ERR_ARG, "NULL argument");
+  if (st->rt == 0) return CSVD_OK;
+  if (ldu < st->rt) return fail(CSVD_ERR_ARG, "ldu < r_eff");
+  CUDA_TRY(cudaMemcpy2DAsync(U_dev, sizeof(float) * ldu, st->U[st->cur], sizeof(float) * st->r,
+                             sizeof(float) * st->rt, st->m, cudaMemcpyDeviceToDevice, st->stream));
+  return CSVD_OK;
+}
+
+csvd_status csvd_tail_error(csvd_state st, double* tail_sq, double* tail_rel,
+                            double* tail_sq_paper, double* energy) {
+  if (!st) return fail(CSVD_ERR_ARG, "state is NULL");
+  double h[2] = {0, 0};
+  std::vector<float> sg(std::max(st->rt, 1));
+  CUDA_TRY(cudaMemcpyAsync(h, st->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, st->stream));
+  if (st->rt > 0)
+    CUDA_TRY(cudaMemcpyAsync(sg.data(), st->sigma, sizeof(float) * st->rt,
+                             cudaMemcpyDeviceToHost, st->stream));
+  CSVD_TRY(take_status(st->status, st->stream));
+  if (tail_sq) *tail_sq = h[1];
+  if (tail_rel) *tail_rel = h[0] > 0 ? std::sqrt(h[1] / h[0]) : 0.0;
+  if (tail_sq_paper) {
+    double top = 0.0;
+    for (int i = 0; i < st->rt; ++i) top += (double)sg[i] * (double)sg[i];
+    *tail_sq_paper = std::max(0.0, h[0] - top);
+  }
+  if (energy) *energy = h[0];
+  return CSVD_OK;
+}
+
+csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
+                       const csvd_block* cands, int32_t n, double eps, int32_t precision,
+                       float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                       double* tail_paper_out, uint8_t* accept_out) {
+  if (!states || n_states < 1 || !cands || n < 0 || !sigma_out || !tail_sq_out)
+    return fail(CSVD_ERR_ARG, "NULL argument");
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+    return fail(CSVD_ERR_ARG, "bad precision");
+  if (n == 0) return CSVD_OK;
+  const int64_t m = states[0]->m;
+  cudaStream_t s = states[0]->stream;
+  std::vector<Item> items(n);
+  for (int i = 0; i < n; ++i) {
+    const int si = cand_state ? cand_state[i] : 0;
+    if (si < 0 || si >= n_states || !states[si]) return fail(CSVD_ERR_ARG, "bad cand_state");
+    if (states[si]->m != m) return fail(CSVD_ERR_SHAPE, "states differ in m");
+    CSVD_TRY(check_block(&cands[i], m));
+    if (ld_sigma < states[si]->r) return fail(CSVD_ERR_ARG, "ld_sigma < r");
+    items[i] = Item{view_of(states[si]), &cands[i], states[si]->r, m, sigma_out + (int64_t)i * ld_sigma,
+                    tail_sq_out + i, tail_paper_out ? tail_paper_out + i : nullptr, nullptr,
+                    accept_out ? accept_out + i : nullptr};
+  }
+  Workspace ws;
+  return run_items(items, eps, precision, s, states[0]->status, ws, nullptr, false);
+}
+
+}  // extern "C"
+
+// ====================================================== internal helpers
+// Empty-state view (r_t = 0) used for per-block spectra.
+static StateView empty_view(const double* zero_scal) {
+  return StateView{nullptr, 1, 0, 0, nullptr, zero_scal};
+}
+
+// Per-block top-r energies, energies and spectra via empty-state evaluations.
+static csvd_status block_spectra(const csvd_block* blocks, const std::vector<int>& idx, int64_t m,
+                                 int r, int precision, cudaStream_t s, int* d_status,
+                                 std::vector<double>& energy, std::vector<double>& top,
+                                 std::vector<std::vector<float>>* spectra) {
+  const int n = (int)idx.size();
+  energy.assign(n, 0.0);
+  top.assign(n, 0.0);
+  if (spectra) spectra->assign(n, {});
+  if (n == 0) return CSVD_OK;
+  Layout L;
+  const size_t o_z = L.add(sizeof(double) * 4);
+  const size_t o_sig = L.add(sizeof(float) * (size_t)n * r);
+  const size_t o_t = L.add(sizeof(double) * n);
+  const size_t o_e = L.add(sizeof(double) * n);
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  CUDA_TRY(cudaMemsetAsync(w.base + o_z, 0, sizeof(double) * 4, s));
+  std::vector<Item> items(n);
+  for (int i = 0; i < n; ++i)
+    items[i] = Item{empty_view(w.at<double>(o_z)), &blocks[idx[i]], r, m, w.at<float>(o_sig) + (size_t)i * r,
+                    w.at<double>(o_t) + i, nullptr, w.at<double>(o_e) + i, nullptr};
+  Workspace ws;
+  CSVD_TRY(run_items(items, 0.0, precision, s, d_status, ws, nullptr, false));
+  std::vector<double> tl(n);
+  std::vector<float> sg((size_t)n * r);
+  CUDA_TRY(cudaMemcpyAsync(tl.data(), w.base + o_t, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(energy.data(), w.base + o_e, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (spectra)
+    CUDA_TRY(cudaMemcpyAsync(sg.data(), w.base + o_sig, sizeof(float) * n * r, cudaMemcpyDeviceToHost, s));
+  CSVD_TRY(take_status(d_status, s));
+  for (int i = 0; i < n; ++i) {
+    top[i] = std::max(0.0, energy[i] - tl[i]);
+    if (spectra) {
+      const int rn = (int)std::min<int64_t>({(int64_t)r, blocks[idx[i]].k, m});
+      (*spectra)[i].assign(sg.begin() + (size_t)i * r, sg.begin() + (size_t)i * r + rn);
+    }
+  }
+  return CSVD_OK;
+}
+
+// ||A_j||_F^2 for the listed blocks (host result).
+static csvd_status block_energies(const csvd_block* blocks, const std::vector<int>& idx, int64_t m,
+                                  cudaStream_t s, std::vector<double>& out) {
+  const int n = (int)idx.size();
+  out.assign(n, 0.0);
+  if (n == 0) return CSVD_OK;
+  std::vector<EnergyDesc> ed(n);
+  Layout L;
+  const size_t o_e = L.add(sizeof(double) * n);
+  const size_t o_d = L.add(sizeof(EnergyDesc) * n);
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  int chunks = 1;
+  for (int i = 0; i < n; ++i) {
+    const csvd_block& b = blocks[idx[i]];
+    ed[i] = EnergyDesc{b.ptr, b.ld, (int)m, (int)b.k, b.dtype == CSVD_BF16, 0, w.at<double>(o_e) + i};
+    chunks = std::max<int>(chunks, (int)std::min<int64_t>(64, (m * b.k + 8191) / 8192));
+  }
+  CUDA_TRY(cudaMemsetAsync(w.base + o_e, 0, sizeof(double) * n, s));
+  CUDA_TRY(upload(w.base + o_d, ed.data(), sizeof(EnergyDesc) * n, s));
+  CUDA_TRY(launch_energy(w.at<EnergyDesc>(o_d), n, chunks, s));
+  CUDA_TRY(cudaMemcpyAsync(out.data(), w.base + o_e, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CSVD_OK;
+}
+
+// Full-span residual state of Alg. 2 / Cor. 1: basis Qf (m x rho, row-major ld m).
+struct SpanState {
+  int64_t m = 0;
+  int rho = 0;
+  float* Qf = nullptr;        // m x m capacity, ld = m
+  double energy = 0.0;
+  std::vector<double> mu;     // residual singular values (multiset)
+  ~SpanState() { cudaFree(Qf); }
+};
+
+// R_j = (I - Qf Qf^T) A_j (one re-orthogonalisation pass) for several blocks,
+// written row-major into `R` (each m x k_j, ld k_j, consecutive).
+static csvd_status span_residuals(const SpanState& sp, const csvd_block* blocks,
+                                  const std::vector<int>& idx, cudaStream_t s, Workspace& w,
+                                  std::vector<csvd_block>& out) {
+  const int n = (int)idx.size();
+  Layout L;
+  std::vector<size_t> oR(n), oP(n), oP2(n);
+  for (int i = 0; i < n; ++i) {
+    const int k = (int)blocks[idx[i]].k;
+    oR[i] = L.add(sizeof(float) * (size_t)sp.m * k);
+    oP[i] = L.add(sizeof(float) * (size_t)std::max(sp.rho, 1) * k);
+    oP2[i] = L.add(sizeof(float) * (size_t)std::max(sp.rho, 1) * k);
+  }
+  GemmBatch g1, g2, g3, g4;
+  auto fill = [&](char* base) {
+    g1 = GemmBatch(); g2 = GemmBatch(); g3 = GemmBatch(); g4 = GemmBatch();
+    for (int i = 0; i < n; ++i) {
+      const csvd_block& b = blocks[idx[i]];
+      const int k = (int)b.k;
+      float* R = reinterpret_cast<float*>(base + oR[i]);
+      float* P = reinterpret_cast<float*>(base + oP[i]);
+      float* P2 = reinterpret_cast<float*>(base + oP2[i]);
+      if (sp.rho > 0) g1.add(gemm(sp.Qf, sp.m, 1, b.ptr, b.ld, 0, P, k, 0, sp.rho, k, (int)sp.m));
+      g2.add(gemm(sp.Qf, sp.m, 0, P, k, 0, R, k, 0, (int)sp.m, k, sp.rho, -1.f,
+                  reinterpret_cast<const float*>(b.ptr), b.ld, 0, 1.f));
+      if (sp.rho > 0) {
+        g3.add(gemm(sp.Qf, sp.m, 1, R, k, 0, P2, k, 0, sp.rho, k, (int)sp.m));
+        g4.add(gemm(sp.Qf, sp.m, 0, P2, k, 0, R, k, 0, (int)sp.m, k, sp.rho, -1.f, R, k, 0, 1.f));
+      }
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  g1.pack(probe); g2.pack(probe); g3.pack(probe); g4.pack(probe);
+  const size_t o_desc = L.add(probe.buf.size());
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  g1.pack(pk); g2.pack(pk); g3.pack(pk); g4.pack(pk);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(g1.launch(dbase, s));
+  CUDA_TRY(g2.launch(dbase, s));
+  CUDA_TRY(g3.launch(dbase, s));
+  CUDA_TRY(g4.launch(dbase, s));
+  out.resize(n);
+  for (int i = 0; i < n; ++i)
+    out[i] = csvd_block{w.base + oR[i], blocks[idx[i]].k, blocks[idx[i]].k, CSVD_F32, 0};
+  return CSVD_OK;
+}
+
+// Extend Qf by the left singular vectors of R whose singular values exceed
+// tol (rank-revealing step of Thm. 2's full-span basis).
+static csvd_status span_extend(SpanState& sp, const csvd_block& R, const std::vector<float>& sv,
+                               double tol, cudaStream_t s) {
+  int q = 0;
+  while (q < (int)sv.size() && (double)sv[q] > tol && sp.rho + q < sp.m) ++q;
+  if (q == 0) return CSVD_OK;
+  csvd_state tmp = nullptr;
+  const int rk = (int)std::min<int64_t>(R.k, sp.m);
+  CSVD_TRY(csvd_incr_init(&tmp, sp.m, rk, CSVD_PLAIN_FP32, s));
+  csvd_status st = append_commit(tmp, &R);
+  if (st == CSVD_OK) {
+    q = std::min(q, tmp->rt);
+    cudaError_t e = cudaMemcpy2DAsync(sp.Qf + sp.rho, sizeof(float) * sp.m, tmp->U[tmp->cur],
+                                      sizeof(float) * tmp->r, sizeof(float) * q, sp.m,
+                                      cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = fail(CSVD_ERR_CUDA, cudaGetErrorString(e));
+    sp.rho += q;
+  }
+  csvd_incr_free(tmp);
+  return st;
+}
+
+static double top_r_sum_sq(std::vector<double> v, int r) {
+  std::sort(v.begin(), v.end(), std::greater<double>());
+  double t = 0.0;
+  for (int i = 0; i < r && i < (int)v.size(); ++i) t += v[i] * v[i];
+  return t;
+}
+
+extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
+                                   void* cuda_stream, double* weyl_sq, double* residual_sq,
+                                   double* plugin_sq, double* energy) {
+  if (!blocks || n < 1 || m < 1 || r < 1 || r > m) return fail(CSVD_ERR_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "bounds take f32 blocks");
+  }
+  int* d_status = nullptr;
+  CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  std::vector<int> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  std::vector<double> en, top;
+  csvd_status st = block_spectra(blocks, all, m, r, CSVD_PLAIN_FP32, s, d_status, en, top, nullptr);
+  double S = 0.0, tmax = 0.0;
+  for (int i = 0; i < n; ++i) { S += en[i]; tmax = std::max(tmax, top[i]); }
+  if (st == CSVD_OK && energy) *energy = S;
+  if (st == CSVD_OK && weyl_sq) *weyl_sq = std::max(0.0, S - tmax);
+  if (st == CSVD_OK && residual_sq) {
+    SpanState sp;
+    sp.m = m;
+    cudaError_t e = cudaMalloc(&sp.Qf, sizeof(float) * m * m);
+    if (e != cudaSuccess) st = fail(CSVD_ERR_OOM, "span basis allocation failed");
+    double Ssofar = 0.0;
+    for (int i = 0; i < n && st == CSVD_OK; ++i) {
+      Workspace w;
+      std::vector<csvd_block> R;
+      st = span_residuals(sp, blocks, {i}, s, w, R);
+      if (st != CSVD_OK) break;
+      std::vector<double> e1, t1;
+      std::vector<std::vector<float>> sv;
+      const int rk = (int)std::min<int64_t>(blocks[i].k, m);
+      st = block_spectra(R.data(), {0}, m, rk, CSVD_PLAIN_FP32, s, d_status, e1, t1, &sv);
+      if (st != CSVD_OK) break;
+      for (float x : sv[0]) sp.mu.push_back(x);
+      Ssofar += en[i];
+      st = span_extend(sp, R[0], sv[0], 1e-6 * std::sqrt(Ssofar), s);
+    }
+    if (st == CSVD_OK) *residual_sq = std::max(0.0, S - top_r_sum_sq(sp.mu, r));
+  }
+  if (st == CSVD_OK && plugin_sq) {
+    csvd_state inc = nullptr;
+    st = csvd_incr_init(&inc, m, r, CSVD_PLAIN_FP32, s);
+    for (int i = 0; i < n && st == CSVD_OK; ++i) st = csvd_incr_append(inc, &blocks[i]);
+    if (st == CSVD_OK) st = csvd_tail_error(inc, plugin_sq, nullptr, nullptr, nullptr);
+    csvd_incr_free(inc);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(d_status);
+  return st;
+}
+
+// ================================================================ clustering
+namespace {
+
+struct Driver {
+  const csvd_block* blocks;
+  int n;
+  int64_t m;
+  int r;
+  double eps;
+  int precision;
+  cudaStream_t s;
+  int* d_status;
+  std::vector<double> norms;   // ||A_j||^2
+  std::vector<int> widths;
+};
+
+// Score candidates `cand` against an incremental state; returns E~^2 and
+// the post-merge energies (host).
+csvd_status score_state(Driver& D, csvd_state st, const std::vector<int>& cand,
+                        std::vector<double>& tail, std::vector<double>& energy) {
+  const int n = (int)cand.size();
+  tail.assign(n, 0.0);
+  energy.assign(n, 0.0);
+  if (n == 0) return CSVD_OK;
+  Layout L;
+  const size_t o_sig = L.add(sizeof(float) * (size_t)n * st->r);
+  const size_t o_t = L.add(sizeof(double) * n);
+  const size_t o_e = L.add(sizeof(double) * n);
+  Workspace w;
+  w.s = D.s;
+  w.base = static_cast<char*>(dev_alloc(L.size, D.s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  std::vector<Item> items(n);
+  for (int i = 0; i < n; ++i)
+    items[i] = Item{view_of(st), &D.blocks[cand[i]], st->r, D.m, w.at<float>(o_sig) + (size_t)i * st->r,
+                    w.at<double>(o_t) + i, nullptr, w.at<double>(o_e) + i, nullptr};
+  {
+    Workspace ws;
+    CSVD_TRY(run_items(items, D.eps, D.precision, D.s, D.d_status, ws, nullptr, false));
+  }
+  CUDA_TRY(cudaMemcpyAsync(tail.data(), w.base + o_t, sizeof(double) * n, cudaMemcpyDeviceToHost, D.s));
+  CUDA_TRY(cudaMemcpyAsync(energy.data(), w.base + o_e, sizeof(double) * n, cudaMemcpyDeviceToHost, D.s));
+  return take_status(D.d_status, D.s);
+}
+
+// Residual norms ||(I - U U^T) A_j||^2 against an incremental state's basis.
+csvd_status residual_norms_state(Driver& D, csvd_state st, const std::vector<int>& cand,
+                                 std::vector<double>& out) {
+  const int n = (int)cand.size();
+  out.assign(n, 0.0);
+  if (n == 0) return CSVD_OK;
+  Layout L;
+  std::vector<size_t> oR(n), oP(n), oP2(n);
+  for (int i = 0; i < n; ++i) {
+    const int k = (int)D.blocks[cand[i]].k;
+    oR[i] = L.add(sizeof(float) * (size_t)D.m * k);
+    oP[i] = L.add(sizeof(float) * (size_t)std::max(st->rt, 1) * k);
+    oP2[i] = L.add(sizeof(float) * (size_t)std::max(st->rt, 1) * k);
+  }
+  const size_t o_en = L.add(sizeof(double) * n);
+  GemmBatch g1, g2, g3, g4;
+  std::vector<EnergyDesc> ed;
+  const float* U = st->U[st->cur];
+  const int64_t ldu = st->r;
+  auto fill = [&](char* base) {
+    g1 = GemmBatch(); g2 = GemmBatch(); g3 = GemmBatch(); g4 = GemmBatch();
+    ed.clear();
+    for (int i = 0; i < n; ++i) {
+      const csvd_block& b = D.blocks[cand[i]];
+      const int k = (int)b.k;
+      float* R = reinterpret_cast<float*>(base + oR[i]);
+      float* P = reinterpret_cast<float*>(base + oP[i]);
+      float* P2 = reinterpret_cast<float*>(base + oP2[i]);
+      if (st->rt > 0) g1.add(gemm(U, ldu, 1, b.ptr, b.ld, 0, P, k, 0, st->rt, k, (int)D.m));
+      g2.add(gemm(U, ldu, 0, P, k, 0, R, k, 0, (int)D.m, k, st->rt, -1.f,
+                  reinterpret_cast<const float*>(b.ptr), b.ld, 0, 1.f));
+      if (st->rt > 0) {
+        g3.add(gemm(U, ldu, 1, R, k, 0, P2, k, 0, st->rt, k, (int)D.m));
+        g4.add(gemm(U, ldu, 0, P2, k, 0, R, k, 0, (int)D.m, k, st->rt, -1.f, R, k, 0, 1.f));
+      }
+      ed.push_back(EnergyDesc{R, k, (int)D.m, k, 0, 0, reinterpret_cast<double*>(base + o_en) + i});
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  g1.pack(probe); g2.pack(probe); g3.pack(probe); g4.pack(probe);
+  probe.add(ed);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = D.s;
+  w.base = static_cast<char*>(dev_alloc(L.size, D.s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  g1.pack(pk); g2.pack(pk); g3.pack(pk); g4.pack(pk);
+  const size_t o_ed = pk.add(ed);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), D.s));
+  CUDA_TRY(cudaMemsetAsync(w.base + o_en, 0, sizeof(double) * n, D.s));
+  CUDA_TRY(g1.launch(dbase, D.s));
+  CUDA_TRY(g2.launch(dbase, D.s));
+  CUDA_TRY(g3.launch(dbase, D.s));
+  CUDA_TRY(g4.launch(dbase, D.s));
+  CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, 16, D.s));
+  CUDA_TRY(cudaMemcpyAsync(out.data(), w.base + o_en, sizeof(double) * n, cudaMemcpyDeviceToHost, D.s));
+  CUDA_TRY(cudaStreamSynchronize(D.s));
+  return CSVD_OK;
+}
+
+std::vector<int> sorted_by(const std::vector<int>& ids, const std::vector<double>& key) {
+  std::vector<int> o(ids.size());
+  std::iota(o.begin(), o.end(), 0);
+  std::stable_sort(o.begin(), o.end(), [&](int a, int b) {
+    if (key[a] != key[b]) return key[a] < key[b];
+    return ids[a] < ids[b];
+  });
+  std::vector<int> out(ids.size());
+  for (size_t i = 0; i < o.size(); ++i) out[i] = ids[o[i]];
+  return out;
+}
+
+// Alg. 3: approximate incremental clustering.
+csvd_status cluster_approx(Driver& D, int sort_mode, std::vector<std::vector<int>>& clusters,
+                           std::vector<double>& est) {
+  std::vector<int> remaining(D.n);
+  std::iota(remaining.begin(), remaining.end(), 0);
+  std::stable_sort(remaining.begin(), remaining.end(), [&](int a, int b) {
+    if (D.norms[a] != D.norms[b]) return D.norms[a] > D.norms[b];
+    return a < b;
+  });
+  while (!remaining.empty()) {
+    const int anchor = remaining.front();
+    remaining.erase(remaining.begin());
+    csvd_state st = nullptr;
+    CSVD_TRY(csvd_incr_init(&st, D.m, D.r, D.precision, D.s));
+    std::vector<int> members{anchor};
+    csvd_status rc = append_commit(st, &D.blocks[anchor]);
+    const double e2 = D.eps * D.eps;
+    while (rc == CSVD_OK && !remaining.empty()) {
+      if (sort_mode == CSVD_SORT_FROBENIUS) {
+        // one scan in ascending norm; batched scores, first accept commits
+        std::vector<double> key(remaining.size());
+        for (size_t i = 0; i < remaining.size(); ++i) key[i] = D.norms[remaining[i]];
+        std::vector<int> order = sorted_by(remaining, key);
+        bool any = false;
+        size_t pos = 0;
+        while (pos < order.size() && rc == CSVD_OK) {
+          std::vector<int> cand(order.begin() + pos, order.end());
+          std::vector<double> tail, energy;
+          rc = score_state(D, st, cand, tail, energy);
+          if (rc != CSVD_OK) break;
+          size_t hit = cand.size();
+          for (size_t i = 0; i < cand.size(); ++i)
+            if (tail[i] <= e2 * energy[i]) { hit = i; break; }
+          if (hit == cand.size()) break;
+          rc = append_commit(st, &D.blocks[cand[hit]]);
+          members.push_back(cand[hit]);
+          remaining.erase(std::find(remaining.begin(), remaining.end(), cand[hit]));
+          any = true;
+          pos += hit + 1;
+        }
+        if (!any) break;
+      } else {
+        std::vector<double> res;
+        rc = residual_norms_state(D, st, remaining, res);
+        if (rc != CSVD_OK) break;
+        std::vector<int> order = sorted_by(remaining, res);
+        std::vector<double> tail, energy;
+        rc = score_state(D, st, order, tail, energy);
+        if (rc != CSVD_OK) break;
+        size_t hit = order.size();
+        for (size_t i = 0; i < order.size(); ++i)
+          if (tail[i] <= e2 * energy[i]) { hit = i; break; }
+        if (hit == order.size()) break;
+        rc = append_commit(st, &D.blocks[order[hit]]);
+        members.push_back(order[hit]);
+        remaining.erase(std::find(remaining.begin(), remaining.end(), order[hit]));
+      }
+    }
+    double tail = 0.0;
+    if (rc == CSVD_OK) rc = csvd_tail_error(st, &tail, nullptr, nullptr, nullptr);
+    csvd_incr_free(st);
+    if (rc != CSVD_OK) return rc;
+    clusters.push_back(members);
+    est.push_back(tail);
+  }
+  return CSVD_OK;
+}
+
+// Alg. 2: residual clustering with a full-span basis.
+csvd_status cluster_residual(Driver& D, int sort_mode, std::vector<std::vector<int>>& clusters,
+                             std::vector<double>& est) {
+  std::vector<int> remaining(D.n);
+  std::iota(remaining.begin(), remaining.end(), 0);
+  std::stable_sort(remaining.begin(), remaining.end(), [&](int a, int b) {
+    if (D.norms[a] != D.norms[b]) return D.norms[a] > D.norms[b];
+    return a < b;
+  });
+  const double e2 = D.eps * D.eps;
+  while (!remaining.empty()) {
+    const int anchor = remaining.front();
+    remaining.erase(remaining.begin());
+    SpanState sp;
+    sp.m = D.m;
+    CUDA_TRY(cudaMalloc(&sp.Qf, sizeof(float) * D.m * D.m));
+    std::vector<int> members{anchor};
+    // anchor: residual against the empty span is the block itself
+    {
+      std::vector<double> e1, t1;
+      std::vector<std::vector<float>> sv;
+      const int rk = (int)std::min<int64_t>(D.blocks[anchor].k, D.m);
+      CSVD_TRY(block_spectra(D.blocks, {anchor}, D.m, rk, CSVD_PLAIN_FP32, D.s, D.d_status, e1, t1, &sv));
+      for (float x : sv[0]) sp.mu.push_back(x);
+      sp.energy = D.norms[anchor];
+      CSVD_TRY(span_extend(sp, D.blocks[anchor], sv[0], 1e-6 * std::sqrt(sp.energy), D.s));
+    }
+    bool grew = true;
+    while (grew && !remaining.empty()) {
+      grew = false;
+      // residuals and their spectra for all remaining blocks against the span
+      Workspace w;
+      std::vector<csvd_block> R;
+      CSVD_TRY(span_residuals(sp, D.blocks, remaining, D.s, w, R));
+      std::vector<int> ridx(remaining.size());
+      std::iota(ridx.begin(), ridx.end(), 0);
+      int rmax = 1;
+      for (auto& b : R) rmax = std::max<int>(rmax, (int)std::min<int64_t>(b.k, D.m));
+      std::vector<double> ren, rtop;
+      std::vector<std::vector<float>> sv;
+      CSVD_TRY(block_spectra(R.data(), ridx, D.m, rmax, CSVD_PLAIN_FP32, D.s, D.d_status, ren, rtop, &sv));
+      std::vector<double> bound(remaining.size()), energy(remaining.size());
+      for (size_t i = 0; i < remaining.size(); ++i) {
+        std::vector<double> mu = sp.mu;
+        for (float x : sv[i]) mu.push_back(x);
+        energy[i] = sp.energy + D.norms[remaining[i]];
+        bound[i] = std::max(0.0, energy[i] - top_r_sum_sq(mu, D.r));
+      }
+      std::vector<double> key(remaining.size());
+      for (size_t i = 0; i < remaining.size(); ++i)
+        key[i] = sort_mode == CSVD_SORT_FROBENIUS ? D.norms[remaining[i]] : ren[i];
+      std::vector<int> pos(remaining.size());
+      std::iota(pos.begin(), pos.end(), 0);
+      std::stable_sort(pos.begin(), pos.end(), [&](int a, int b) {
+        if (key[a] != key[b]) return key[a] < key[b];
+        return remaining[a] < remaining[b];
+      });
+      for (int p : pos) {
+        if (bound[p] <= e2 * energy[p]) {
+          const int j = remaining[p];
+          for (float x : sv[p]) sp.mu.push_back(x);
+          sp.energy = energy[p];
+          CSVD_TRY(span_extend(sp, R[p], sv[p], 1e-6 * std::sqrt(sp.energy), D.s));
+          members.push_back(j);
+          remaining.erase(remaining.begin() + p);
+          grew = true;
+          break;  // the span changed: residuals of the others are recomputed
+        }
+      }
+    }
+    clusters.push_back(members);
+    est.push_back(std::max(0.0, sp.energy - top_r_sum_sq(sp.mu, D.r)));
+  }
+  return CSVD_OK;
+}
+
+// Alg. 1: max-norm (Weyl) clustering with a head of width <= r.
+csvd_status cluster_weyl(Driver& D, std::vector<std::vector<int>>& clusters,
+                         std::vector<double>& est) {
+  std::vector<int> all(D.n);
+  std::iota(all.begin(), all.end(), 0);
+  std::vector<double> en, top;
+  CSVD_TRY(block_spectra(D.blocks, all, D.m, D.r, D.precision, D.s, D.d_status, en, top, nullptr));
+  std::vector<int> desc = all;
+  std::stable_sort(desc.begin(), desc.end(), [&](int a, int b) {
+    if (D.norms[a] != D.norms[b]) return D.norms[a] > D.norms[b];
+    return a < b;
+  });
+  std::vector<int> remaining = desc;
+  const double e2 = D.eps * D.eps;
+  while (!remaining.empty()) {
+    const int anchor = remaining.front();
+    remaining.erase(remaining.begin());
+    std::vector<int> members{anchor};
+    bool head = false;
+    double S = D.norms[anchor], Shead = 0.0, tmax = top[anchor];
+    if (D.widths[anchor] <= D.r) {
+      head = true;
+      int width = D.widths[anchor];
+      Shead = D.norms[anchor];
+      while (!remaining.empty() && width + D.widths[remaining.front()] <= D.r) {
+        const int j = remaining.front();
+        remaining.erase(remaining.begin());
+        members.push_back(j);
+        width += D.widths[j];
+        S += D.norms[j];
+        Shead += D.norms[j];
+      }
+    }
+    while (true) {
+      std::vector<double> key(remaining.size());
+      for (size_t i = 0; i < remaining.size(); ++i) key[i] = D.norms[remaining[i]];
+      std::vector<int> order = sorted_by(remaining, key);
+      bool any = false;
+      for (int j : order) {
+        const double S2 = S + D.norms[j];
+        double b;
+        double t2 = tmax;
+        if (head) b = S2 - Shead;
+        else { t2 = std::max(tmax, top[j]); b = S2 - t2; }
+        b = std::max(0.0, b);
+        if (b <= e2 * S2) {
+          S = S2;
+          tmax = t2;
+          members.push_back(j);
+          remaining.erase(std::find(remaining.begin(), remaining.end(), j));
+          any = true;
+        }
+      }
+      if (!any || remaining.empty()) break;
+    }
+    clusters.push_back(members);
+    est.push_back(std::max(0.0, head ? S - Shead : S - tmax));
+  }
+  return CSVD_OK;
+}
+
+}  // namespace
+
+extern "C" csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
+                                    double eps, int32_t algo, int32_t sort_mode, int32_t precision,
+                                    void* cuda_stream, int32_t* labels_out,
+                                    double* cluster_est_sq_out, double* energy_out,
+                                    double* compression_ratio_out) {
+  if (!blocks || n < 1 || m < 1 || r < 1 || r > m || !labels_out || !(eps >= 0.0))
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  if (algo != CSVD_ALG_WEYL && algo != CSVD_ALG_RESIDUAL && algo != CSVD_ALG_APPROX)
+    return fail(CSVD_ERR_ARG, "bad algo");
+  if (sort_mode != CSVD_SORT_FROBENIUS && sort_mode != CSVD_SORT_RESIDUAL)
+    return fail(CSVD_ERR_ARG, "bad sort mode");
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+    return fail(CSVD_ERR_ARG, "bad precision");
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "clustering takes f32 blocks");
+  }
+  Driver D;
+  D.blocks = blocks;
+  D.n = n;
+  D.m = m;
+  D.r = r;
+  D.eps = eps;
+  D.precision = precision;
+  D.s = static_cast<cudaStream_t>(cuda_stream);
+  CUDA_TRY(cudaMalloc(&D.d_status, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(D.d_status, 0, sizeof(int), D.s));
+  std::vector<int> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  D.widths.resize(n);
+  for (int i = 0; i < n; ++i) D.widths[i] = (int)blocks[i].k;
+  // block energies
+  csvd_status rc;
+  rc = block_energies(blocks, all, m, D.s, D.norms);
+  std::vector<std::vector<int>> clusters;
+  std::vector<double> est;
+  if (rc == CSVD_OK) {
+    if (algo == CSVD_ALG_APPROX) rc = cluster_approx(D, sort_mode, clusters, est);
+    else if (algo == CSVD_ALG_RESIDUAL) rc = cluster_residual(D, sort_mode, clusters, est);
+    else rc = cluster_weyl(D, clusters, est);
+  }
+  cudaStreamSynchronize(D.s);
+  cudaFree(D.d_status);
+  if (rc != CSVD_OK) return rc;
+  int64_t raw = 0, stored = 0;
+  for (size_t c = 0; c < clusters.size(); ++c) {
+    int64_t nc = 0;
+    double en = 0.0;
+    for (int j : clusters[c]) {
+      labels_out[j] = (int32_t)c;
+      nc += D.widths[j];
+      en += D.norms[j];
+    }
+    if (cluster_est_sq_out) cluster_est_sq_out[c] = est[c];
+    if (energy_out) energy_out[c] = en;
+    const int64_t reff = std::min<int64_t>({(int64_t)r, nc, m});
+    raw += m * nc;
+    stored += std::min<int64_t>(m * nc, reff * (m + nc));
+  }
+  for (size_t c = clusters.size(); c < (size_t)n; ++c) {
+    if (cluster_est_sq_out) cluster_est_sq_out[c] = 0.0;
+    if (energy_out) energy_out[c] = 0.0;
+  }
+  if (compression_ratio_out) *compression_ratio_out = (double)raw / (double)stored;
+  return CSVD_OK;
+}
+
+extern "C" csvd_status csvd_tail_grad(const float* U, int64_t ldu, int64_t m, int32_t r,
+                                      const csvd_block* blocks, const csvd_block* grads,
+                                      int32_t n, double g, void* cuda_stream) {
+  if (!U || !blocks || !grads || n < 0 || m < 1 || r < 0 || ldu < r)
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    CSVD_TRY(check_block(&grads[i], m));
+    if (blocks[i].dtype != CSVD_F32 || grads[i].dtype != CSVD_F32 || grads[i].k != blocks[i].k)
+      return fail(CSVD_ERR_ARG, "gradients take f32 blocks of the same width");
+  }
+  if (n == 0) return CSVD_OK;
+  Layout L;
+  std::vector<size_t> oP(n);
+  for (int i = 0; i < n; ++i) oP[i] = L.add(sizeof(float) * (size_t)std::max(r, 1) * blocks[i].k);
+  GemmBatch g1, g2;
+  auto fill = [&](char* base) {
+    g1 = GemmBatch(); g2 = GemmBatch();
+    for (int i = 0; i < n; ++i) {
+      const int k = (int)blocks[i].k;
+      float* P = reinterpret_cast<float*>(base + oP[i]);
+      if (r > 0) g1.add(gemm(U, ldu, 1, blocks[i].ptr, blocks[i].ld, 0, P, k, 0, r, k, (int)m));
+      g2.add(gemm(U, ldu, 0, P, k, 0, const_cast<float*>(reinterpret_cast<const float*>(grads[i].ptr)),
+                  grads[i].ld, 0, (int)m, k, r, (float)(-2.0 * g),
+                  reinterpret_cast<const float*>(blocks[i].ptr), blocks[i].ld, 0, (float)(2.0 * g)));
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  g1.pack(probe); g2.pack(probe);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  g1.pack(pk); g2.pack(pk);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(g1.launch(dbase, s));
+  CUDA_TRY(g2.launch(dbase, s));
+  return CSVD_OK;
+}
+
+extern "C" csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m,
+                                         void* cuda_stream, double* energy_host) {
+  if (!blocks || n < 0 || m < 1 || !energy_host) return fail(CSVD_ERR_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i) CSVD_TRY(check_block(&blocks[i], m));
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::vector<double> out;
+  CSVD_TRY(block_energies(blocks, idx, m, static_cast<cudaStream_t>(cuda_stream), out));
+  for (int i = 0; i < n; ++i) energy_host[i] = out[i];
+  return CSVD_OK;
+}
+
+extern "C" int64_t csvd_launch_count(void) { return (int64_t)g_launch_count.load(); }
+
+extern "C" csvd_status csvd_profile(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& e : g_prof) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g_prof.clear();
+  g_prof_on.store(enable != 0);
+  return CSVD_OK;
+}
+
+extern "C" csvd_status csvd_profile_report(char* buf, int64_t len) {
+  if (!buf || len < 1) return fail(CSVD_ERR_ARG, "bad buffer");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  struct Acc { std::string name; long long n = 0; double ms = 0.0; };
+  std::vector<Acc> acc;
+  for (auto& e : g_prof) {
+    cudaError_t err = cudaEventSynchronize(e.b);
+    if (err != cudaSuccess) return fail(CSVD_ERR_CUDA, cudaGetErrorString(err));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    auto it = std::find_if(acc.begin(), acc.end(), [&](const Acc& a) { return a.name == e.name; });
+    if (it == acc.end()) { acc.push_back(Acc{e.name, 0, 0.0}); it = acc.end() - 1; }
+    it->n += 1;
+    it->ms += ms;
+  }
+  std::string out;
+  for (auto& a : acc) out += a.name + " " + std::to_string(a.n) + " " + std::to_string(a.ms) + "\n";
+  std::snprintf(buf, (size_t)len, "%s", out.c_str());
+  return CSVD_OK;
+}

@@ -1,0 +1,438 @@
+// The small core of a merge evaluation, its truncation and the tail
+// estimate (Lemma 1, Cor. 3 and Cor. 2), plus the block-energy reduction.
+//
+// Two core solvers, one CTA per item:
+//  * core_jacobi_kernel (plain form): one-sided (Hestenes) Jacobi on the
+//    columns of K = [[diag(s), P], [0, B]] (n_r = r_t + kp rows, n_c = r_t + k
+//    columns).  Disjoint column pairs of a round-robin schedule are rotated
+//    by separate warps; column norms at convergence are the singular values
+//    and the normalised columns the left singular vectors.
+//  * core_tridiag_kernel (mixed form): the eigenvalues of the Gram
+//    K^T K = [[S, diag(s) P], [P^T diag(s), A^T A]] (n = r_t + k), whose
+//    nonzero eigenvalues are those of K K^T = S_{t+1}: Householder
+//    tridiagonalisation (warp-per-row symmetric matrix-vector products,
+//    block-wide rank-2 updates), then one bisection per eigenvalue on the
+//    Sturm count of the tridiagonal matrix.
+// Both finish with the same FP64 epilogue: sigma~ = top r_new values, the
+// tail as accumulated discarded energy (equal to sum ||A||^2 - sum sigma~^2
+// in exact arithmetic, without its cancellation) and the merge certificate
+// tail <= eps^2 ||M_{C u j}||^2 (Alg. 3 step 3(e)).
+// The core lives in shared memory when it fits, else in a global workspace.
+#include "common.cuh"
+
+namespace csvd {
+
+constexpr int kJacobiMaxSweeps = 40;
+constexpr int kBisectMaxIter = 64;
+
+// ------------------------------------------------------------- energy
+__global__ void __launch_bounds__(256)
+energy_kernel(const EnergyDesc* __restrict__ descs) {
+  __shared__ double red[8];
+  const EnergyDesc d = descs[blockIdx.y];
+  const int64_t total = (int64_t)d.m * d.k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float s = 0.f, comp = 0.f;  // Kahan-compensated FP32 partial
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t i = e / d.k, c = e % d.k;
+    const float a = load_elem(d.A, i * d.ld + c, d.bf16);
+    const float y = fmaf(a, a, -comp);
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+  }
+  double v = warp_sum_d((double)s - (double)comp);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(d.out, t);
+  }
+}
+
+cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
+                          cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid(max_chunks < 1 ? 1 : max_chunks, n_items);
+  prof_begin(s);
+  energy_kernel<<<grid, 256, 0, s>>>(d_desc);
+  prof_end("block_energy", s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ shared epilogue
+// vals[0..nv) non-increasing; writes sigma~, tails and the accept flag.
+// Called by warp 0 only; vals_are_sq says whether vals hold sigma^2.
+__device__ void core_epilogue(const CoreDesc& d, const float* vals, int nv, bool vals_are_sq) {
+  const int lane = threadIdx.x & 31;
+  double top = 0.0, disc = 0.0;
+  for (int q = lane; q < nv; q += 32) {
+    const double x = vals[q];
+    const double sq = vals_are_sq ? x : x * x;
+    if (q < d.r_new) top += sq; else disc += sq;
+    if (q < d.r_new)
+      d.sigma_out[q] = vals_are_sq ? sqrtf(fmaxf(vals[q], 0.f)) : vals[q];
+  }
+  top = warp_sum_d(top);
+  disc = warp_sum_d(disc);
+  if (lane == 0) {
+    const double energy_new = d.scal[0] + d.energy_add[0];
+    double tail = d.scal[1] + disc;
+    if (tail < 0.0) tail = 0.0;
+    double paper = energy_new - top;
+    if (paper < 0.0) paper = 0.0;
+    d.tail_out[0] = tail;
+    if (d.tail_paper_out) d.tail_paper_out[0] = paper;
+    if (d.energy_out) d.energy_out[0] = energy_new;
+    if (d.accept_out) d.accept_out[0] = (tail <= d.eps * d.eps * energy_new) ? 1 : 0;
+  }
+}
+
+// --------------------------------------------------------- Jacobi core
+__device__ __forceinline__ void rr_pair(int t, int p, int n, int& a, int& b) {
+  if (p == 0) { a = n - 1; b = t; }
+  else { a = (t + p) % (n - 1); b = (t - p + (n - 1)) % (n - 1); }
+}
+
+__global__ void __launch_bounds__(1024)
+core_jacobi_kernel(const CoreDesc* __restrict__ descs, int* __restrict__ status) {
+  extern __shared__ __align__(16) float smem[];
+  const CoreDesc d = descs[blockIdx.x];
+  const int nr = d.rt + d.kp, nc = d.rt + d.k;
+  const int ncp = nc + (nc & 1);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  float* norms = smem;                                  // ncp
+  int* order = reinterpret_cast<int*>(smem + ncp);      // ncp
+  float* svals = smem + 2 * ncp;                        // ncp
+  __shared__ int s_rot;
+  const int scratch = ((3 * ncp + 3) / 4) * 4;
+  float* K = d.in_smem ? smem + scratch : d.work;
+  const int64_t ldk = d.in_smem ? nr : d.ldwork;
+
+  // assemble K column-major
+  for (int64_t e = tid; e < (int64_t)ncp * nr; e += blockDim.x) {
+    const int c = (int)(e / nr), i = (int)(e % nr);
+    float v = 0.f;
+    if (c < d.rt) v = (i == c) ? d.sigma[c] : 0.f;
+    else if (c < nc) {
+      const int cc = c - d.rt;
+      if (i < d.rt) {
+        v = d.P[(int64_t)i * d.ldp + cc];
+        if (d.P2) v += d.P2[(int64_t)i * d.ldp + cc];
+      } else {
+        v = d.B[(int64_t)(i - d.rt) * d.ldb + cc];
+      }
+    }
+    K[(int64_t)c * ldk + i] = v;
+  }
+  __syncthreads();
+
+  const float tol = 4.f * 5.9604645e-8f * sqrtf((float)(nr > 1 ? nr : 1));
+  bool converged = (ncp < 2);
+  for (int sweep = 0; sweep < kJacobiMaxSweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int t = 0; t < ncp - 1; ++t) {
+      for (int p = wid; p < ncp / 2; p += nw) {
+        int a, b;
+        rr_pair(t, p, ncp, a, b);
+        if (a >= nc || b >= nc) continue;
+        float* x = K + (int64_t)a * ldk;
+        float* y = K + (int64_t)b * ldk;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < nr; i += 32) {
+          const float xi = x[i], yi = y[i];
+          al = fmaf(xi, xi, al);
+          be = fmaf(yi, yi, be);
+          ga = fmaf(xi, yi, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        const float scale = sqrtf(al) * sqrtf(be);
+        if (!(scale > 1e-36f) || !(fabsf(ga) > tol * scale)) continue;
+        const float zeta = (be - al) / (2.f * ga);
+        float tt;
+        if (fabsf(zeta) > 1e7f) tt = 0.5f / zeta;
+        else tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+        const float sn = cs * tt;
+        for (int i = lane; i < nr; i += 32) {
+          const float xi = x[i], yi = y[i];
+          x[i] = cs * xi - sn * yi;
+          y[i] = fmaf(sn, xi, cs * yi);
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    converged = (s_rot == 0);
+    __syncthreads();
+  }
+  if (!converged && tid == 0) atomicOr(status, kStatusJacobiCap);
+
+  // column norms = singular values, sorted non-increasing (ties: index)
+  for (int c = wid; c < nc; c += nw) {
+    const float* x = K + (int64_t)c * ldk;
+    float s = 0.f;
+    for (int i = lane; i < nr; i += 32) s = fmaf(x[i], x[i], s);
+    s = warp_sum(s);
+    if (lane == 0) norms[c] = sqrtf(s);
+  }
+  __syncthreads();
+  for (int c = tid; c < nc; c += blockDim.x) {
+    const float v = norms[c];
+    int rank = 0;
+    for (int e = 0; e < nc; ++e) {
+      const float u = norms[e];
+      rank += (u > v) || (u == v && e < c);
+    }
+    order[rank] = c;
+  }
+  __syncthreads();
+  for (int q = tid; q < nc; q += blockDim.x) svals[q] = norms[order[q]];
+  __syncthreads();
+  if (wid == 0) core_epilogue(d, svals, nc, false);
+  if (d.Wt) {
+    for (int64_t e = tid; e < (int64_t)d.r_new * nr; e += blockDim.x) {
+      const int j = (int)(e / nr), i = (int)(e % nr);
+      const float s = svals[j];
+      const float v = K[(int64_t)order[j] * ldk + i];
+      d.Wt[(int64_t)j * d.ldw + i] = s > 0.f ? v / s : 0.f;
+    }
+  }
+}
+
+int jacobi_scratch_floats(int nc) {
+  const int ncp = nc + (nc & 1);
+  return ((3 * ncp + 3) / 4) * 4;
+}
+
+cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
+                               int* d_status, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (smem_bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(core_jacobi_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(s);
+  core_jacobi_kernel<<<n_items, 1024, smem_bytes, s>>>(d_desc, d_status);
+  prof_end("core_jacobi", s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- tridiagonal Gram core
+__device__ __forceinline__ int sturm_count(const float* dv, const float* e2, int n, float x,
+                                           float pivmin) {
+  float q = dv[0] - x;
+  int cnt = q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    if (fabsf(q) < pivmin) q = -pivmin;
+    q = (dv[i] - x) - e2[i - 1] / q;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(1024)
+core_tridiag_kernel(const CoreDesc* __restrict__ descs, int* __restrict__ status) {
+  extern __shared__ __align__(16) float smem[];
+  const CoreDesc d = descs[blockIdx.x];
+  const int n = d.rt + d.k;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  float* dv = smem;             // n diagonal
+  float* ev = dv + n;           // n off-diagonal (e[i] couples i, i+1)
+  float* vv = ev + n;           // n reflector
+  float* pv = vv + n;           // n p / w
+  float* lam = pv + n;          // n eigenvalues, non-increasing
+  float* red = lam + n;         // 64 floats
+  const int scratch = ((5 * n + 64 + 3) / 4) * 4;
+  float* G = d.in_smem ? smem + scratch : d.work;
+  const int64_t ld = d.in_smem ? n : d.ldwork;
+  __shared__ float s_beta, s_tau2, s_skip;
+
+  // assemble the Gram core K^T K
+  for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    float v;
+    if (i < d.rt && j < d.rt) v = (i == j) ? d.sigma[i] * d.sigma[i] : 0.f;
+    else if (i < d.rt) v = d.sigma[i] * d.P[(int64_t)i * d.ldp + (j - d.rt)];
+    else if (j < d.rt) v = d.sigma[j] * d.P[(int64_t)j * d.ldp + (i - d.rt)];
+    else {
+      const int a = min(i, j) - d.rt, b = max(i, j) - d.rt;
+      v = d.Gaa[(int64_t)a * d.ldb + b];
+    }
+    G[(int64_t)i * ld + j] = v;
+  }
+  __syncthreads();
+
+  // Householder tridiagonalisation: G <- H G H, H = I - tau2 v v^T
+  for (int j = 0; j + 2 < n; ++j) {
+    const int t = n - j - 1;
+    const float* row = G + (int64_t)j * ld + (j + 1);
+    float part = 0.f;
+    for (int l = 1 + tid; l < t; l += blockDim.x) part = fmaf(row[l], row[l], part);
+    const float tail2 = block_sum(part, red);
+    const float x0 = row[0];
+    if (tid == 0) {
+      dv[j] = G[(int64_t)j * ld + j];
+      if (tail2 == 0.f) {
+        ev[j] = x0;
+        s_skip = 1.f;
+      } else {
+        const float nrm = sqrtf(fmaf(x0, x0, tail2));
+        const float beta = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - beta;
+        ev[j] = beta;
+        s_beta = v0;
+        s_tau2 = 2.f / fmaf(v0, v0, tail2);
+        s_skip = 0.f;
+      }
+    }
+    __syncthreads();
+    if (s_skip != 0.f) { __syncthreads(); continue; }
+    const float tau2 = s_tau2;
+    for (int l = tid; l < t; l += blockDim.x) vv[l] = (l == 0) ? s_beta : row[l];
+    __syncthreads();
+    // p = tau2 * G_t v  (warp per row)
+    for (int i = wid; i < t; i += nw) {
+      const float* gr = G + (int64_t)(j + 1 + i) * ld + (j + 1);
+      float acc = 0.f;
+      for (int l = lane; l < t; l += 32) acc = fmaf(gr[l], vv[l], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) pv[i] = tau2 * acc;
+    }
+    __syncthreads();
+    float pp = 0.f;
+    for (int l = tid; l < t; l += blockDim.x) pp = fmaf(pv[l], vv[l], pp);
+    const float kk = 0.5f * tau2 * block_sum(pp, red);
+    for (int l = tid; l < t; l += blockDim.x) pv[l] = fmaf(-kk, vv[l], pv[l]);
+    __syncthreads();
+    // G_t -= v w^T + w v^T
+    for (int64_t e = tid; e < (int64_t)t * t; e += blockDim.x) {
+      const int i = (int)(e / t), l = (int)(e % t);
+      float* g = G + (int64_t)(j + 1 + i) * ld + (j + 1 + l);
+      *g = fmaf(-vv[i], pv[l], fmaf(-pv[i], vv[l], *g));
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dv[n - 2] = G[(int64_t)(n - 2) * ld + (n - 2)];
+      ev[n - 2] = G[(int64_t)(n - 1) * ld + (n - 2)];
+    }
+    dv[n - 1] = G[(int64_t)(n - 1) * ld + (n - 1)];
+    ev[n - 1] = 0.f;
+  }
+  __syncthreads();
+  // squared off-diagonal, Gershgorin interval
+  float lo = 3.0e38f, hi = -3.0e38f, emax = 0.f;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const float el = i > 0 ? fabsf(ev[i - 1]) : 0.f;
+    const float er = i + 1 < n ? fabsf(ev[i]) : 0.f;
+    lo = fminf(lo, dv[i] - el - er);
+    hi = fmaxf(hi, dv[i] + el + er);
+    emax = fmaxf(emax, er * er);
+  }
+  __shared__ float s_lo[32], s_hi[32], s_em[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
+  if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; s_em[wid] = emax; }
+  __syncthreads();
+  float glo = s_lo[0], ghi = s_hi[0], gem = s_em[0];
+  for (int w = 1; w < nw; ++w) {
+    glo = fminf(glo, s_lo[w]);
+    ghi = fmaxf(ghi, s_hi[w]);
+    gem = fmaxf(gem, s_em[w]);
+  }
+  // reuse vv as e^2
+  for (int i = tid; i < n; i += blockDim.x) vv[i] = (i + 1 < n) ? ev[i] * ev[i] : 0.f;
+  __syncthreads();
+  const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
+  const float pivmin = 1.0e-30f * fmaxf(1.f, gem);
+  const float atol = 2.4e-7f * gnorm + 1e-30f;
+  int capped = 0;
+  for (int q = tid; q < n; q += blockDim.x) {
+    const int target = n - 1 - q;  // ascending index of the q-th largest
+    float a = glo, b = ghi;
+    int it = 0;
+    for (; it < kBisectMaxIter; ++it) {
+      const float mid = 0.5f * (a + b);
+      if (!(mid > a && mid < b) || (b - a) <= atol) break;
+      if (sturm_count(dv, vv, n, mid, pivmin) > target) b = mid; else a = mid;
+    }
+    if (it == kBisectMaxIter) capped = 1;
+    lam[q] = 0.5f * (a + b);
+  }
+  if (capped) atomicOr(status, kStatusBisectCap);
+  __syncthreads();
+  if (wid == 0) {
+    // eigenvalues beyond rt + kp are zero in exact arithmetic (rank <= m)
+    core_epilogue(d, lam, n, true);
+  }
+}
+
+int tridiag_scratch_floats(int n) { return ((5 * n + 64 + 3) / 4) * 4; }
+
+cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes,
+                                int* d_status, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (smem_bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(s);
+  core_tridiag_kernel<<<n_items, 1024, smem_bytes, s>>>(d_desc, d_status);
+  prof_end("core_tridiag", s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ small helpers
+__global__ void state_commit_kernel(const float* sigma_new, int r_new, float* sigma,
+                                    const double* energy_new, const double* tail_new,
+                                    double* scal) {
+  for (int i = threadIdx.x; i < r_new; i += blockDim.x) sigma[i] = sigma_new[i];
+  if (threadIdx.x == 0) {
+    scal[0] = energy_new[0];
+    scal[1] = tail_new[0];
+  }
+}
+
+cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
+                                const double* energy_new, const double* tail_new,
+                                double* scal, cudaStream_t s) {
+  prof_begin(s);
+  state_commit_kernel<<<1, 256, 0, s>>>(sigma_new, r_new, sigma, energy_new, tail_new, scal);
+  prof_end("state_commit", s);
+  return cudaGetLastError();
+}
+
+__global__ void add_inplace_kernel(float* dst, const float* src, int rows, int cols,
+                                   int64_t ld_dst, int64_t ld_src) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    dst[i * ld_dst + j] += src[i * ld_src + j];
+  }
+}
+
+cudaError_t launch_add_inplace(float* dst, const float* src, int rows, int cols,
+                               int64_t ld_dst, int64_t ld_src, cudaStream_t s) {
+  const int64_t total = (int64_t)rows * cols;
+  if (total <= 0) return cudaSuccess;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  prof_begin(s);
+  add_inplace_kernel<<<blocks, 256, 0, s>>>(dst, src, rows, cols, ld_dst, ld_src);
+  prof_end("add_inplace", s);
+  return cudaGetLastError();
+}
+
+}  // namespace csvd

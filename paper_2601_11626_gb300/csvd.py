@@ -1,0 +1,334 @@
+"""Thin ctypes binding of the csvd C ABI (``include/csvd.h``).
+
+Argument marshalling only: torch tensors supply device memory and the
+current CUDA stream; every step of the computation runs in the library's
+kernels.  There is no CPU fallback: ``lib()`` raises when the CUDA library
+is missing or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import enum
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+_LIB = None
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    ERR_ARG = 1
+    ERR_SHAPE = 2
+    ERR_CUDA = 3
+    ERR_OOM = 4
+    ERR_NOT_CONVERGED = 5
+    ERR_TIMEOUT = 6
+    ERR_UNIMPLEMENTED = 7
+
+
+PLAIN, MIXED = 0, 1
+ALGO = {"weyl": 1, "residual": 2, "approx": 3}
+SORT = {"frobenius": 0, "residual": 1}
+F32, BF16 = 0, 1
+
+
+class CsvdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"csvd: {Status(status).name}: {msg}")
+        self.status = Status(status)
+
+
+class Block(C.Structure):
+    _fields_ = [("ptr", C.c_void_p), ("k", C.c_int64), ("ld", C.c_int64),
+                ("dtype", C.c_int32), ("reserved", C.c_int32)]
+
+
+def _sig(lib):
+    P, I32, I64, D, VP = C.POINTER, C.c_int32, C.c_int64, C.c_double, C.c_void_p
+    lib.csvd_last_error.restype = C.c_char_p
+    lib.csvd_version.restype = C.c_char_p
+    lib.csvd_incr_init.argtypes = [P(VP), I64, I32, I32, VP]
+    lib.csvd_incr_append.argtypes = [VP, P(Block)]
+    lib.csvd_incr_sigma.argtypes = [VP, P(C.c_float), P(I32)]
+    lib.csvd_incr_basis.argtypes = [VP, VP, I64]
+    lib.csvd_tail_error.argtypes = [VP, P(D), P(D), P(D), P(D)]
+    lib.csvd_incr_free.argtypes = [VP]
+    lib.csvd_score.argtypes = [P(VP), I32, P(I32), P(Block), I32, D, I32, VP, I64, VP, VP, VP]
+    lib.csvd_bounds.argtypes = [P(Block), I32, I64, I32, VP, P(D), P(D), P(D), P(D)]
+    lib.csvd_cluster.argtypes = [P(Block), I32, I64, I32, D, I32, I32, I32, VP, P(I32), P(D),
+                                 P(D), P(D)]
+    lib.csvd_tail_grad.argtypes = [VP, I64, I64, I32, P(Block), P(Block), I32, D, VP]
+    lib.csvd_block_energy.argtypes = [P(Block), I32, I64, VP, P(D)]
+    lib.csvd_set_allocator.argtypes = [VP, VP, VP]
+    lib.csvd_launch_count.restype = C.c_int64
+    lib.csvd_profile.argtypes = [I32]
+    lib.csvd_profile.restype = C.c_int
+    lib.csvd_profile_report.argtypes = [C.c_char_p, I64]
+    lib.csvd_profile_report.restype = C.c_int
+    for name in ("csvd_incr_init", "csvd_incr_append", "csvd_incr_sigma", "csvd_incr_basis",
+                 "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_bounds",
+                 "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator"):
+        getattr(lib, name).restype = C.c_int
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(require_gpu: bool = True):
+    """Load libcsvd.so (built by ``__graft_entry__.build()``)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"csvd CUDA library not built: {path} is missing")
+        l = C.CDLL(path)
+        _sig(l)
+        _LIB = l
+    if require_gpu and not torch.cuda.is_available():
+        raise RuntimeError("csvd needs a CUDA GPU; none is available")
+    return _LIB
+
+
+def _check(st):
+    if st != 0:
+        raise CsvdError(st, lib(False).csvd_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def block(t: torch.Tensor) -> Block:
+    """Descriptor of a row-major (m, k) CUDA tensor (f32 or bf16, unit
+    column stride)."""
+    if not t.is_cuda or t.dim() != 2:
+        raise ValueError("blocks must be 2-D CUDA tensors")
+    if t.stride(1) != 1 and t.shape[1] > 1:
+        raise ValueError("blocks need unit column stride (row-major)")
+    if t.dtype == torch.float32:
+        dt = F32
+    elif t.dtype == torch.bfloat16:
+        dt = BF16
+    else:
+        raise ValueError("blocks must be float32 or bfloat16")
+    ld = t.stride(0) if t.shape[0] > 1 else t.shape[1]
+    return Block(t.data_ptr(), t.shape[1], max(ld, t.shape[1]), dt, 0)
+
+
+def _blocks(ts):
+    arr = (Block * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = block(t)
+    return arr
+
+
+class IncrSVD:
+    """Rank-r incremental truncated SVD state (Lemma 1, Cor. 3)."""
+
+    def __init__(self, m: int, r: int, precision: str = "plain", stream=None):
+        self._lib = lib()
+        self.m, self.r = m, r
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(self._lib.csvd_incr_init(C.byref(h), m, r, MIXED if precision == "mixed" else PLAIN,
+                                        _stream(self.stream)))
+        self._h = h
+        self._keep = []
+
+    def append(self, A: torch.Tensor):
+        b = block(A)
+        _check(self._lib.csvd_incr_append(self._h, C.byref(b)))
+        self._keep.append(A)  # borrowed until the stream reaches it
+        if len(self._keep) > 64:
+            self.stream.synchronize()
+            self._keep.clear()
+        return self
+
+    def sigma(self) -> np.ndarray:
+        out = (C.c_float * self.r)()
+        reff = C.c_int32()
+        _check(self._lib.csvd_incr_sigma(self._h, out, C.byref(reff)))
+        self._keep.clear()
+        return np.frombuffer(out, dtype=np.float32, count=reff.value).copy()
+
+    @property
+    def rank(self) -> int:
+        reff = C.c_int32()
+        _check(self._lib.csvd_incr_sigma(self._h, None, C.byref(reff)))
+        return reff.value
+
+    def basis(self) -> torch.Tensor:
+        rk = self.rank
+        U = torch.empty(self.m, max(rk, 1), device="cuda", dtype=torch.float32)
+        _check(self._lib.csvd_incr_basis(self._h, C.c_void_p(U.data_ptr()), U.stride(0)))
+        return U[:, :rk]
+
+    def tail_error(self) -> dict:
+        t, rel, paper, en = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        _check(self._lib.csvd_tail_error(self._h, C.byref(t), C.byref(rel), C.byref(paper),
+                                         C.byref(en)))
+        self._keep.clear()
+        return dict(tail_sq=t.value, tail_rel=rel.value, tail_sq_paper=paper.value,
+                    energy=en.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.csvd_incr_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ScoreBatch:
+    """Prepared descriptor arrays for repeated ``csvd_score`` calls on the
+    same candidates (avoids rebuilding ctypes arrays inside timed loops)."""
+
+    def __init__(self, states, cand_state, cands, eps, precision="mixed", r_max=None):
+        self._lib = lib()
+        self.states = states
+        self.n = len(cands)
+        self.eps = float(eps)
+        self.precision = MIXED if precision == "mixed" else PLAIN
+        self._st = (C.c_void_p * len(states))(*[s.handle.value for s in states])
+        self._cs = (C.c_int32 * self.n)(*[int(x) for x in cand_state])
+        self._cb = _blocks(cands)
+        self.cands = cands
+        self.r_max = r_max or max(s.r for s in states)
+        self.sigma = torch.zeros(self.n, self.r_max, device="cuda", dtype=torch.float32)
+        self.tail = torch.zeros(self.n, device="cuda", dtype=torch.float64)
+        self.paper = torch.zeros(self.n, device="cuda", dtype=torch.float64)
+        self.accept = torch.zeros(self.n, device="cuda", dtype=torch.uint8)
+
+    def run(self):
+        _check(self._lib.csvd_score(self._st, len(self.states), self._cs, self._cb, self.n,
+                                    self.eps, self.precision,
+                                    C.c_void_p(self.sigma.data_ptr()), self.r_max,
+                                    C.c_void_p(self.tail.data_ptr()),
+                                    C.c_void_p(self.paper.data_ptr()),
+                                    C.c_void_p(self.accept.data_ptr())))
+        return self
+
+
+def score(states, cand_state, cands, eps, precision="mixed"):
+    """Batched merge evaluations; returns (sigma, tail_sq, tail_paper, accept)
+    as CUDA tensors."""
+    b = ScoreBatch(states, cand_state, cands, eps, precision).run()
+    return b.sigma, b.tail, b.paper, b.accept
+
+
+def block_energy(blocks):
+    m = blocks[0].shape[0]
+    out = (C.c_double * len(blocks))()
+    _check(lib().csvd_block_energy(_blocks(blocks), len(blocks), m, _stream(), out))
+    return np.frombuffer(out, dtype=np.float64).copy()
+
+
+def bounds(blocks, r):
+    """Weyl (Thm. 1), residual (Cor. 1) and plug-in (Cor. 2) values and the
+    energy, for the blocks in the given order."""
+    m = blocks[0].shape[0]
+    w, res, plug, en = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib().csvd_bounds(_blocks(blocks), len(blocks), m, r, _stream(), C.byref(w),
+                             C.byref(res), C.byref(plug), C.byref(en)))
+    return dict(weyl_sq=w.value, residual_sq=res.value, plugin_sq=plug.value, energy=en.value)
+
+
+def cluster(blocks, r, eps, algo="approx", sort_mode="frobenius", precision="plain"):
+    """Algorithms 1-3 (Appendix E).  Returns labels, clusters (members in
+    label order), per-cluster certificate values, energies and the
+    compression ratio."""
+    n = len(blocks)
+    m = blocks[0].shape[0]
+    labels = (C.c_int32 * n)()
+    est = (C.c_double * n)()
+    en = (C.c_double * n)()
+    ratio = C.c_double()
+    _check(lib().csvd_cluster(_blocks(blocks), n, m, r, float(eps), ALGO[algo], SORT[sort_mode],
+                              MIXED if precision == "mixed" else PLAIN, _stream(), labels, est,
+                              en, C.byref(ratio)))
+    lab = list(labels)
+    k = max(lab) + 1
+    return dict(labels=lab, n_clusters=k, estimate_sq=list(est)[:k], energy=list(en)[:k],
+                compression_ratio=ratio.value)
+
+
+def tail_grad(U: torch.Tensor, blocks, g: float = 1.0):
+    """dA_j = 2 g (I - U U^T) A_j for every block (new f32 tensors)."""
+    m = blocks[0].shape[0]
+    grads = [torch.empty_like(b, dtype=torch.float32) for b in blocks]
+    U = U.contiguous() if U.stride(1) != 1 else U
+    _check(lib().csvd_tail_grad(C.c_void_p(U.data_ptr()), U.stride(0), m, U.shape[1],
+                                _blocks(blocks), _blocks(grads), len(blocks), float(g),
+                                _stream()))
+    return grads
+
+
+def _basis(blocks, r, working_rank):
+    st = IncrSVD(blocks[0].shape[0], working_rank or r)
+    for b in blocks:
+        st.append(b)
+    U = st.basis()[:, :r].contiguous()
+    st.close()
+    return U
+
+
+class TailEnergy(torch.autograd.Function):
+    """E = sum_j ||(I - U_r U_r^T) A_j||_F^2 with U_r the top-r basis from the
+    incremental estimator; backward dA_j = 2 (I - U_r U_r^T) A_j * gE
+    (the Eckart-Young tail gradient, valid when sigma_r > sigma_{r+1}).  U_r
+    is recomputed in the backward instead of being stored."""
+
+    @staticmethod
+    def forward(ctx, r, working_rank, *blocks):
+        U = _basis(blocks, r, working_rank)
+        res = tail_grad(U, list(blocks), 0.5)
+        e = block_energy(res).sum()
+        ctx.r, ctx.working_rank = r, working_rank
+        ctx.save_for_backward(*blocks)
+        return torch.tensor(e, dtype=torch.float64, device=blocks[0].device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        blocks = ctx.saved_tensors
+        U = _basis(blocks, ctx.r, ctx.working_rank)
+        grads = tail_grad(U, list(blocks), float(gE))
+        return (None, None, *grads)
+
+
+def tail_energy(blocks, r, working_rank=None):
+    return TailEnergy.apply(r, working_rank, *blocks)
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib(False).csvd_launch_count())
+
+
+def profile(enable: bool):
+    _check(lib(False).csvd_profile(1 if enable else 0))
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total device ms)} from the CUDA events
+    recorded on each launch stream since ``profile(True)``."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib(False).csvd_profile_report(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out

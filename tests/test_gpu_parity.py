@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (derived from FP32 arithmetic):
+* sigma~ (plain form): |d sigma_j| <= 1e-5 sigma_j + 2e-6 sigma_1.  The second
+  term is the normwise floor of FP32 products (~30 u sigma_1): a singular
+  value far below sigma_1 cannot be resolved better than that from FP32
+  data by any FP32 method.
+* sigma~ (mixed form, eigenvalues of the Gram): |d sigma_j^2| <= 1e-4
+  sigma_j^2 + 2e-6 sigma_1^2 (the Gram squares the floor).
+* tail E~ (both forms): 1e-4 relative on E~ = sqrt(E~^2).
+* accept flags identical except for merges whose relative estimate lies
+  within 1e-3 (relative) of eps; those are listed.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bounds as obounds
+from oracle import cluster as ocluster
+from oracle import exact as oexact
+from oracle import incremental as oinc
+from paper_2601_11626_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TAIL_RTOL = 1e-4
+
+
+def _np(t):
+    return t.detach().cpu().double().numpy()
+
+
+def _check_sigma(got, want, mixed=False):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    if want.size == 0:
+        return
+    s1 = want[0]
+    if mixed:
+        err = np.abs(got ** 2 - want ** 2)
+        bound = 1e-4 * want ** 2 + 2e-6 * s1 ** 2
+    else:
+        err = np.abs(got - want)
+        bound = 1e-5 * want + 2e-6 * s1
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"sigma mismatch at {bad[:8]}: got {got[bad[:8]]} want {want[bad[:8]]}"
+
+
+def _check_tail(got_sq, want_sq, rtol=TAIL_RTOL, floor=0.0):
+    g, w = math.sqrt(max(got_sq, 0.0)), math.sqrt(max(want_sq, 0.0))
+    assert abs(g - w) <= rtol * w + floor, (g, w, abs(g - w) / max(w, 1e-300))
+
+
+@pytest.fixture(scope="module")
+def csvd(cuda_lib):
+    from paper_2601_11626_gb300 import csvd as mod
+    return mod
+
+
+# ------------------------------------------------------- incremental append
+def test_incremental_small_every_step(csvd):
+    col = synth.small_c1()
+    r = col.meta["r"]
+    st = csvd.IncrSVD(col.m, r)
+    ost = oinc.IncrementalSVD(col.m, r)
+    for b in col.blocks:
+        st.append(b.cuda())
+        ost.append(b)
+        _check_sigma(st.sigma(), ost.s)
+        t = st.tail_error()
+        _check_tail(t["tail_sq"], ost.tail_sq_discard())
+        assert math.isclose(t["energy"], ost.energy, rel_tol=1e-6)
+    U = _np(st.basis())
+    assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-4
+
+
+def test_incremental_mid_size(csvd):
+    col = synth.mid_c2(n_blocks=12)
+    r = col.meta["r"]
+    st = csvd.IncrSVD(col.m, r)
+    ost = oinc.IncrementalSVD(col.m, r)
+    for b in col.blocks:
+        st.append(b.cuda())
+        ost.append(b)
+    _check_sigma(st.sigma(), ost.s)
+    _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard())
+
+
+@pytest.mark.parametrize("m,widths,r", [
+    (32, [1, 1, 1, 1, 1], 3),          # k = 1 (rank-one appends)
+    (16, [2, 2, 2], 12),                # r above the total rank
+    (32, [24, 24, 24], 16),             # r_t + k > m: kp = m - r_t
+    (40, [7, 33, 5, 64], 9),            # ragged widths, k > m
+    (64, [130], 64),                    # single block wider than two GEMM tiles
+])
+def test_incremental_edge_shapes(csvd, m, widths, r):
+    blocks = synth.random_blocks(m, widths, seed=3, decay=0.8)
+    st = csvd.IncrSVD(m, r)
+    ost = oinc.IncrementalSVD(m, r)
+    for b in blocks:
+        st.append(b.cuda())
+        ost.append(b)
+        _check_sigma(st.sigma(), ost.s)
+        _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard(),
+                    floor=3e-6 * math.sqrt(ost.energy))
+
+
+def test_incremental_padded_leading_dimension(csvd):
+    blocks = synth.random_blocks(48, [5, 9, 13], seed=4, decay=0.9)
+    views, pool = synth.pack_blocks([b.cuda() for b in blocks], ld_align=16)
+    st = csvd.IncrSVD(48, 6)
+    ost = oinc.IncrementalSVD(48, 6)
+    for v, b in zip(views, blocks):
+        assert v.stride(0) == 16
+        st.append(v)
+        ost.append(b)
+    _check_sigma(st.sigma(), ost.s)
+
+
+def test_zero_block(csvd):
+    st = csvd.IncrSVD(20, 4)
+    ost = oinc.IncrementalSVD(20, 4)
+    for b in synth.random_blocks(20, [3], seed=5) + [torch.zeros(20, 4)]:
+        st.append(b.cuda())
+        ost.append(b)
+    _check_sigma(st.sigma(), ost.s)
+    _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard(), floor=1e-6)
+
+
+# -------------------------------------------------------- batched scoring
+def _states(csvd, m, r, groups):
+    gpu, cpu = [], []
+    for blocks in groups:
+        g = csvd.IncrSVD(m, r)
+        c = oinc.IncrementalSVD(m, r)
+        for b in blocks:
+            g.append(b.cuda() if not b.is_cuda else b)
+            c.append(b)
+        gpu.append(g)
+        cpu.append(c)
+    return gpu, cpu
+
+
+def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision):
+    sig, tail, paper, acc = csvd.score(gst, cand_state, cands, eps, precision)
+    sig, tail, paper, acc = _np(sig), _np(tail), _np(paper), acc.cpu().numpy()
+    boundary = []
+    for i, (si, b) in enumerate(zip(cand_state, cands)):
+        s_o, t_o, a_o, nxt = cst[si].evaluate(b.cpu(), eps)
+        _check_sigma(sig[i, :len(s_o)], s_o, mixed=(precision == "mixed"))
+        # the oracle's accumulated-discard form (exactly its paper form in exact arithmetic)
+        _check_tail(tail[i], nxt[3])
+        rel = math.sqrt(t_o / nxt[2])
+        if abs(rel - eps) <= 1e-3 * eps:
+            boundary.append(i)
+        elif bool(acc[i]) != a_o:
+            raise AssertionError(f"accept flag differs at {i}: gpu {acc[i]} oracle {a_o}")
+    return boundary
+
+
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_score_mid_size(csvd, precision):
+    col = synth.mid_c2(n_blocks=40)
+    m, r = col.m, col.meta["r"]
+    groups = [col.blocks[0:4], col.blocks[16:19]]
+    gst, cst = _states(csvd, m, r, groups)
+    cands = [b.cuda() for b in col.blocks[20:36]]
+    cand_state = [i % 2 for i in range(len(cands))]
+    for eps in (0.1, 0.2, 0.3):
+        _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision)
+
+
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_score_uneven_large_cores(csvd, precision):
+    """Uneven widths in [16, 512] at m = 2048: cores up to 576 x 576 take
+    the global-memory path; ragged widths exercise every tile tail."""
+    w = synth.scoring_c4(r=64, n_states=3, appends=3, per_state=5, device="cuda")
+    m, r = w["m"], w["r"]
+    gst, cst = _states(csvd, m, r, w["states"])
+    cands = w["candidates"]
+    ks = [c.shape[1] for c in cands]
+    assert min(ks) < 224 < max(ks)
+    _compare_scores(csvd, gst, cst, w["cand_state"], cands, 0.25, precision)
+
+
+def test_score_empty_state_gives_block_spectrum(csvd):
+    """A first append scored from an empty state is the rank-r SVD of the
+    block (Alg. 3 step 1)."""
+    blocks = synth.random_blocks(64, [20, 37], seed=6, decay=0.85)
+    for precision in ("plain", "mixed"):
+        st = csvd.IncrSVD(64, 10)
+        sig, tail, _, _ = csvd.score([st], [0, 0], [b.cuda() for b in blocks], 0.1, precision)
+        for i, b in enumerate(blocks):
+            s = np.linalg.svd(b.double().numpy(), compute_uv=False)
+            _check_sigma(_np(sig)[i, :10], s[:10], mixed=precision == "mixed")
+            _check_tail(float(tail[i]), float(np.sum(s[10:] ** 2)))
+
+
+def test_score_bf16_blocks_mixed(csvd):
+    blocks = synth.random_blocks(128, [40, 64], seed=7, decay=0.9)
+    bb = [b.to(torch.bfloat16) for b in blocks]
+    st = csvd.IncrSVD(128, 16)
+    sig, tail, _, _ = csvd.score([st], [0, 0], [b.cuda() for b in bb], 0.1, "mixed")
+    for i, b in enumerate(bb):
+        s = np.linalg.svd(b.double().numpy(), compute_uv=False)
+        _check_sigma(_np(sig)[i, :16], s[:16], mixed=True)
+        _check_tail(float(tail[i]), float(np.sum(s[16:] ** 2)))
+
+
+# ----------------------------------------------------------------- bounds
+def test_bounds_small(csvd):
+    col = synth.small_c1()
+    r = col.meta["r"]
+    got = csvd.bounds([b.cuda() for b in col.blocks], r)
+    w, res, plug, en = obounds.all_bounds(col.blocks, r)
+    assert math.isclose(got["energy"], en, rel_tol=1e-6)
+    for key, want in (("weyl_sq", w), ("residual_sq", res), ("plugin_sq", plug)):
+        _check_tail(got[key], want)
+    ex = oexact.tail_sq(col.blocks, r)
+    for key in ("weyl_sq", "residual_sq", "plugin_sq"):
+        assert got[key] >= ex * (1 - 2e-4)
+
+
+# ------------------------------------------------------------- clustering
+def _boundary_in_log(log, eps):
+    for _, _, b2, energy, _ in log:
+        if energy > 0 and abs(math.sqrt(b2 / energy) - eps) <= 1e-3 * eps:
+            return True
+    return False
+
+
+@pytest.mark.parametrize("algo,mode", [("weyl", "frobenius"), ("residual", "frobenius"),
+                                       ("residual", "residual"), ("approx", "frobenius"),
+                                       ("approx", "residual")])
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_cluster_small(csvd, algo, mode, precision):
+    if algo == "residual" and precision == "mixed":
+        pytest.skip("Alg. 2 has no mixed form")
+    col = synth.small_c1()
+    r, eps = col.meta["r"], col.meta["eps"]
+    got = csvd.cluster([b.cuda() for b in col.blocks], r, eps, algo, mode, precision)
+    want = ocluster.cluster(col.blocks, r, eps, algo, mode)
+    want_labels = [0] * len(col.blocks)
+    for c, mem in enumerate(want["clusters"]):
+        for j in mem:
+            want_labels[j] = c
+    if _boundary_in_log(want["log"], eps):
+        pytest.skip("a merge lies within 1e-3 of the threshold (listed by the oracle log)")
+    assert got["labels"] == want_labels
+    assert math.isclose(got["compression_ratio"], want["compression_ratio"], rel_tol=1e-12)
+    for c in range(got["n_clusters"]):
+        _check_tail(got["estimate_sq"][c], want["estimate_sq"][c],
+                    floor=1e-6 * math.sqrt(want["energy"][c]))
+
+
+def test_cluster_mid_size_approx(csvd):
+    col = synth.mid_c2(n_blocks=24)
+    r = col.meta["r"]
+    eps = 0.3
+    got = csvd.cluster([b.cuda() for b in col.blocks], r, eps, "approx", "frobenius", "mixed")
+    want = ocluster.cluster(col.blocks, r, eps, "approx", "frobenius")
+    if _boundary_in_log(want["log"], eps):
+        pytest.skip("boundary merge")
+    want_labels = [0] * len(col.blocks)
+    for c, mem in enumerate(want["clusters"]):
+        for j in mem:
+            want_labels[j] = c
+    assert got["labels"] == want_labels
+
+
+# ------------------------------------------------------------ gradients
+def test_tail_grad_matches_oracle(csvd):
+    w = synth.grad_c5(n_blocks=8, m=256, k=32)
+    blocks = w["fd"]
+    r = 40
+    u, _ = oexact.top_left_basis(blocks, r)
+    U = torch.tensor(u, dtype=torch.float32, device="cuda")
+    got = csvd.tail_grad(U, [b.cuda() for b in blocks], 1.0)
+    want = oexact.tail_grad(blocks, r)
+    for g, wt in zip(got, want):
+        np.testing.assert_allclose(_np(g), wt, atol=2e-5 * np.abs(wt).max())
+
+
+def test_tail_energy_autograd_fd_full_size(csvd):
+    """Config-5 check: 8 blocks 2048 x 256 from three latent subspaces with a
+    large gap at r = 128; backward of the autograd function against central
+    finite differences (h = 1e-3) of the FP64 oracle's exact tail."""
+    w = synth.grad_c5(n_blocks=8)
+    blocks = w["fd"]
+    r = w["r"]
+    s = oexact.singular_values(blocks)
+    assert s[r - 1] / s[r] >= 1.5
+    xs = [b.cuda().requires_grad_(True) for b in blocks]
+    E = csvd.tail_energy(xs, r, working_rank=r + 32)
+    E.backward()
+    assert math.isclose(float(E), oexact.tail_sq(blocks, r), rel_tol=1e-3)
+    rng = np.random.default_rng(0)
+    h = 1e-3
+    for _ in range(3):
+        d = [rng.standard_normal(b.shape) for b in blocks]
+        bp = [b.double().numpy() + h * x for b, x in zip(blocks, d)]
+        bm = [b.double().numpy() - h * x for b, x in zip(blocks, d)]
+        fd = (oexact.tail_sq(bp, r) - oexact.tail_sq(bm, r)) / (2 * h)
+        an = sum(float(np.sum(_np(x.grad) * dd)) for x, dd in zip(xs, d))
+        assert math.isclose(fd, an, rel_tol=1e-3), (fd, an)
+    want = oexact.tail_grad(blocks, r)
+    for x, wt in zip(xs, want):
+        np.testing.assert_allclose(_np(x.grad), wt, atol=1e-3 * np.abs(wt).max())
+
+
+# ------------------------------------------------------------------ errors
+def test_argument_errors_return_status(csvd):
+    st = csvd.IncrSVD(16, 4)
+    bad = csvd.Block(0, 4, 4, 0, 0)
+    import ctypes
+    assert csvd.lib().csvd_incr_append(st.handle, ctypes.byref(bad)) == csvd.Status.ERR_ARG
+    x = torch.zeros(16, 4, device="cuda")
+    b = csvd.block(x)
+    b.ld = 2
+    assert csvd.lib().csvd_incr_append(st.handle, ctypes.byref(b)) == csvd.Status.ERR_ARG
+    b = csvd.block(x)
+    b.dtype = 9
+    assert csvd.lib().csvd_incr_append(st.handle, ctypes.byref(b)) == csvd.Status.ERR_ARG
+    st.append(x)   # still usable after rejected calls
+    assert st.rank == 4

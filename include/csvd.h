@@ -95,6 +95,15 @@ csvd_status csvd_incr_init(csvd_state* out, int64_t m, int32_t r, int32_t precis
  * Stream-ordered, asynchronous.  A->ptr must hold m rows. */
 csvd_status csvd_incr_append(csvd_state s, const csvd_block* A);
 
+/* Replace the state's contents (checkpoint / resume): basis U (m x rt,
+ * row-major, device, leading dimension ldu, orthonormal columns), retained
+ * singular values sigma_host (rt values, non-increasing, host), the energy
+ * sum_i ||A_i||_F^2 and the accumulated discarded energy.  0 <= rt <= r.
+ * A state saved with csvd_incr_basis, csvd_incr_sigma and csvd_tail_error
+ * resumes exactly.  Syncs. */
+csvd_status csvd_incr_load(csvd_state s, const float* U_dev, int64_t ldu, int32_t rt,
+                           const float* sigma_host, double energy, double discarded);
+
 /* Copy the retained singular values sigma~_1..r_eff (Cor. 3, item 2) to
  * host memory (at least r floats) and the current rank.  Syncs. */
 csvd_status csvd_incr_sigma(csvd_state s, float* sigma_host, int32_t* r_eff);
@@ -158,6 +167,16 @@ csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t m, int32_t
 csvd_status csvd_tail_grad(const float* U, int64_t ldu, int64_t m, int32_t r,
                            const csvd_block* blocks, const csvd_block* grads, int32_t n,
                            double g, void* cuda_stream);
+
+/* Y = sum_j A_j (A_j^T U) = M M^T U for the concatenation M of the blocks:
+ * one sweep of subspace iteration, used to refine a basis U (m x r,
+ * row-major, device, ldu) towards the top-r left singular subspace of M
+ * before the tail gradient (the gradient formula needs the exact top-r
+ * basis; each sweep shrinks the angle by sigma_{r+1}^2 / sigma_r^2).
+ * Y is m x r row-major (device, ldy).  Stream-ordered. */
+csvd_status csvd_gram_apply(const float* U, int64_t ldu, int64_t m, int32_t r,
+                            const csvd_block* blocks, int32_t n, float* Y, int64_t ldy,
+                            void* cuda_stream);
 
 /* ||A_j||_F^2 of each block (Kahan-compensated FP32 partial sums, FP64
  * totals) into energy_host[0..n).  Syncs. */

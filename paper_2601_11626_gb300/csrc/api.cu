@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -17,6 +18,7 @@
 
 #include "csvd.h"
 #include "common.cuh"
+#include "tc_gram.cuh"
 
 using namespace csvd;
 
@@ -269,6 +271,35 @@ static csvd_status take_status(int* d_status, cudaStream_t s) {
 
 // Largest core kept in shared memory (bytes of dynamic shared memory).
 static constexpr int kCoreSmemBudget = 200 * 1024;
+// Eigenvalue-core launch classes: small cores share an SM, large cores get
+// (almost) all of its shared memory and spill the leading steps to global.
+static constexpr int kTriSmallN = 160;
+static constexpr int kTriLargeSmem = 220 * 1024;
+
+static int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+// The Gram of the mixed form runs on the tensor cores unless CSVD_GRAM=simt.
+static bool gram_on_tensor_cores() {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = std::getenv("CSVD_GRAM");
+    mode = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
+  }
+  return mode == 1;
+}
+
+static int tri_small_smem(int n_max) {
+  return (6 * n_max + 96 + n_max * (n_max + 1) / 2) * 4 + 64;
+}
 
 // ===================================================== the batched pipeline
 // One merge evaluation per item: (state view, block).  Produces sigma~,
@@ -317,11 +348,9 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
     if (mixed) {
       o.G = L.add(sizeof(float) * (size_t)k * k);
-      const int nn = rt + k;
-      const int need = (tridiag_scratch_floats(nn) + nn * nn) * 4;
-      o.smem = need <= kCoreSmemBudget;
-      o.ldwork = nn;
-      o.work = o.smem ? 0 : L.add(sizeof(float) * (size_t)nn * nn);
+      o.ldwork = rt + k;
+      o.smem = false;
+      o.work = 0;
     } else {
       o.P2 = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
       o.Rt = L.add(sizeof(float) * (size_t)k * m);
@@ -335,15 +364,41 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       o.Wt = want_W ? L.add(sizeof(float) * (size_t)std::max(o.r_new, 1) * o.nr) : 0;
     }
   }
-  // descriptor tables are filled after allocation (they hold device pointers)
-  const size_t energy_lo = off[0].energy;
-  (void)energy_lo;
+  // mixed form: eigen-core classes; cores too large for shared memory get a
+  // packed global workspace for their leading steps
+  int tri_nmax_small = 1, tri_nmax_large = 1;
+  if (mixed) {
+    for (int i = 0; i < n; ++i) {
+      const int nn = items[i].st.rt + (int)items[i].blk->k;
+      if (nn <= kTriSmallN) tri_nmax_small = std::max(tri_nmax_small, nn);
+      else tri_nmax_large = std::max(tri_nmax_large, nn);
+    }
+    const int cap = tridiag_smem_cap(kTriLargeSmem, tri_nmax_large);
+    for (int i = 0; i < n; ++i) {
+      const int nn = items[i].st.rt + (int)items[i].blk->k;
+      off[i].smem = nn <= kTriSmallN;
+      if (!off[i].smem && nn > cap)
+        off[i].work = L.add(sizeof(float) * ((size_t)nn * (nn + 1) / 2));
+    }
+  }
+  // tensor-core Gram: eligible items (f32, 16-byte aligned rows)
+  std::vector<char> tc_ok(n, 0);
+  if (mixed && gram_on_tensor_cores()) {
+    for (int i = 0; i < n; ++i) {
+      const Item& it = items[i];
+      const bool a_ok = it.blk->dtype == CSVD_F32 && (reinterpret_cast<uintptr_t>(it.blk->ptr) & 15) == 0 &&
+                        (it.blk->ld & 3) == 0;
+      const bool u_ok = it.st.rt == 0 || ((reinterpret_cast<uintptr_t>(it.st.U) & 15) == 0 && (it.st.ldu & 3) == 0);
+      tc_ok[i] = a_ok && u_ok;
+    }
+  }
   // upper bound for the descriptor region: computed after building with a dummy base
   // -> build twice: sizes do not depend on the base pointer.
   auto build = [&](char* base, Pack& pk, GemmBatch& gP, GemmBatch& gR, GemmBatch& gP2,
                    GemmBatch& gRu, GemmBatch& gG, std::vector<EnergyDesc>& ed,
                    std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
-                   std::vector<CoreDesc>& cd_g) {
+                   std::vector<CoreDesc>& cd_g, std::vector<TcItem>& tci,
+                   std::vector<TcTile>& tct) {
     int max_m = 1;
     for (int i = 0; i < n; ++i) {
       const Item& it = items[i];
@@ -356,7 +411,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       float* P = rt > 0 ? reinterpret_cast<float*>(base + o.P) : nullptr;
       EnergyDesc e{it.blk->ptr, it.blk->ld, (int)m, k, bf, 0, energy};
       ed.push_back(e);
-      if (rt > 0)
+      if (rt > 0 && !tc_ok[i])
         gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, k, 0, rt, k, (int)m,
                     1.f, nullptr, 0, 0, 0.f, 0, bf));
       CoreDesc c;
@@ -382,10 +437,21 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       c.ldwork = o.ldwork;
       if (mixed) {
         float* G = reinterpret_cast<float*>(base + o.G);
-        gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, k, 0, k, k,
-                    (int)m, 1.f, nullptr, 0, 0, 0.f, bf, bf), true);
+        if (tc_ok[i]) {
+          const int id = (int)tci.size();
+          tci.push_back(TcItem{reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, it.st.U,
+                               it.st.ldu, (int)m, k, rt, 0, P, k, G, k});
+          for (int r0 = 0; r0 < rt; r0 += kTcBM)
+            for (int c0 = 0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 0, r0, c0});
+          for (int r0 = 0; r0 < k; r0 += kTcBM)
+            for (int c0 = r0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 1, r0, c0});
+        } else {
+          gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, k, 0, k, k,
+                      (int)m, 1.f, nullptr, 0, 0, 0.f, bf, bf), true);
+        }
         c.Gaa = G;
         c.ldb = k;
+        c.work = o.work ? reinterpret_cast<float*>(base + o.work) : nullptr;
       } else {
         if (bf) return false;
         float* P2 = rt > 0 ? reinterpret_cast<float*>(base + o.P2) : nullptr;
@@ -415,16 +481,18 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     (void)max_m;
     return true;
   };
+  // the core of an item lands in cd_s (small / on-chip class) or cd_g
   // pass 1: sizes of the descriptor region
   size_t desc_bytes = 0;
   {
     Pack pk;
     GemmBatch a, b, c, d, e;
     std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg;
+    std::vector<TcItem> ti; std::vector<TcTile> tt;
     char* fake = reinterpret_cast<char*>(uintptr_t(1) << 20);
-    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg))
+    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg, ti, tt))
       return fail(CSVD_ERR_UNIMPLEMENTED, "bf16 blocks need the mixed form");
-    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg);
+    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg); pk.add(ti); pk.add(tt);
     desc_bytes = pk.buf.size();
   }
   const size_t off_desc = L.add(desc_bytes);
@@ -434,8 +502,10 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   Pack pk;
   GemmBatch gP, gR, gP2, gRu, gG;
   std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g;
-  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g);
+  std::vector<TcItem> tci; std::vector<TcTile> tct;
+  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g, tci, tct);
   const size_t o_ed = pk.add(ed), o_qd = pk.add(qd), o_cs = pk.add(cd_s), o_cg = pk.add(cd_g);
+  const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);
   char* dbase = ws.base + off_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
   // energies start at zero
@@ -450,13 +520,13 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
   CUDA_TRY(gP.launch(dbase, s));
   if (mixed) {
+    CUDA_TRY(launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti), reinterpret_cast<TcTile*>(dbase + o_tt),
+                            (int)tct.size(), num_sms(), d_status, s));
     CUDA_TRY(gG.launch(dbase, s));
-    int sm = 0;
-    for (auto& c : cd_s) sm = std::max(sm, (tridiag_scratch_floats(c.rt + c.k) + (c.rt + c.k) * (c.rt + c.k)) * 4);
-    int gm = 0;
-    for (auto& c : cd_g) gm = std::max(gm, tridiag_scratch_floats(c.rt + c.k) * 4);
-    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(), sm, d_status, s));
-    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(), gm, d_status, s));
+    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
+                                 kTriLargeSmem, tri_nmax_large, d_status, s));
+    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
+                                 tri_small_smem(tri_nmax_small), tri_nmax_small, d_status, s));
   } else {
     CUDA_TRY(gR.launch(dbase, s));
     CUDA_TRY(gP2.launch(dbase, s));
@@ -596,6 +666,26 @@ csvd_status csvd_incr_append(csvd_state st, const csvd_block* A) {
   CSVD_TRY(check_block(A, st->m));
   if (A->dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "append takes f32 blocks");
   return append_commit(st, A);
+}
+
+csvd_status csvd_incr_load(csvd_state st, const float* U_dev, int64_t ldu, int32_t rt,
+                           const float* sigma_host, double energy, double discarded) {
+  if (!st) return fail(CSVD_ERR_ARG, "state is NULL");
+  if (rt < 0 || rt > st->r || (rt > 0 && (!U_dev || !sigma_host || ldu < rt)))
+    return fail(CSVD_ERR_ARG, "need 0 <= rt <= r, U and sigma for rt > 0, ldu >= rt");
+  if (!(energy >= 0.0) || !(discarded >= 0.0)) return fail(CSVD_ERR_ARG, "negative energy");
+  if (rt > 0) {
+    CUDA_TRY(cudaMemcpy2DAsync(st->U[st->cur], sizeof(float) * st->r, U_dev, sizeof(float) * ldu,
+                               sizeof(float) * rt, st->m, cudaMemcpyDeviceToDevice, st->stream));
+    CUDA_TRY(cudaMemcpyAsync(st->sigma, sigma_host, sizeof(float) * rt, cudaMemcpyHostToDevice,
+                             st->stream));
+  }
+  const double sc[2] = {energy, discarded};
+  CUDA_TRY(cudaMemcpyAsync(st->scal, sc, sizeof(sc), cudaMemcpyHostToDevice, st->stream));
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  st->rt = rt;
+  st->nblocks = rt > 0 ? 1 : 0;
+  return CSVD_OK;
 }
 
 csvd_status csvd_incr_sigma(csvd_state st, float* sigma_host, int32_t* r_eff) {
@@ -748,6 +838,7 @@ struct SpanState {
   int rho = 0;
   float* Qf = nullptr;        // m x m capacity, ld = m
   double energy = 0.0;
+  double proj = 0.0;          // sum_i ||Q_{i-1}^T A_i||^2 over the accepted blocks
   std::vector<double> mu;     // residual singular values (multiset)
   ~SpanState() { cudaFree(Qf); }
 };
@@ -756,7 +847,7 @@ struct SpanState {
 // written row-major into `R` (each m x k_j, ld k_j, consecutive).
 static csvd_status span_residuals(const SpanState& sp, const csvd_block* blocks,
                                   const std::vector<int>& idx, cudaStream_t s, Workspace& w,
-                                  std::vector<csvd_block>& out) {
+                                  std::vector<csvd_block>& out, std::vector<double>& proj) {
   const int n = (int)idx.size();
   Layout L;
   std::vector<size_t> oR(n), oP(n), oP2(n);
@@ -766,9 +857,12 @@ static csvd_status span_residuals(const SpanState& sp, const csvd_block* blocks,
     oP[i] = L.add(sizeof(float) * (size_t)std::max(sp.rho, 1) * k);
     oP2[i] = L.add(sizeof(float) * (size_t)std::max(sp.rho, 1) * k);
   }
+  const size_t o_pe = L.add(sizeof(double) * n);
   GemmBatch g1, g2, g3, g4;
+  std::vector<EnergyDesc> ed;
   auto fill = [&](char* base) {
     g1 = GemmBatch(); g2 = GemmBatch(); g3 = GemmBatch(); g4 = GemmBatch();
+    ed.clear();
     for (int i = 0; i < n; ++i) {
       const csvd_block& b = blocks[idx[i]];
       const int k = (int)b.k;
@@ -781,12 +875,14 @@ static csvd_status span_residuals(const SpanState& sp, const csvd_block* blocks,
       if (sp.rho > 0) {
         g3.add(gemm(sp.Qf, sp.m, 1, R, k, 0, P2, k, 0, sp.rho, k, (int)sp.m));
         g4.add(gemm(sp.Qf, sp.m, 0, P2, k, 0, R, k, 0, (int)sp.m, k, sp.rho, -1.f, R, k, 0, 1.f));
+        ed.push_back(EnergyDesc{P, k, sp.rho, k, 0, 0, reinterpret_cast<double*>(base + o_pe) + i});
       }
     }
   };
   fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
   Pack probe;
   g1.pack(probe); g2.pack(probe); g3.pack(probe); g4.pack(probe);
+  probe.add(ed);
   const size_t o_desc = L.add(probe.buf.size());
   w.s = s;
   w.base = static_cast<char*>(dev_alloc(L.size, s));
@@ -794,12 +890,18 @@ static csvd_status span_residuals(const SpanState& sp, const csvd_block* blocks,
   fill(w.base);
   Pack pk;
   g1.pack(pk); g2.pack(pk); g3.pack(pk); g4.pack(pk);
+  const size_t o_ed = pk.add(ed);
   char* dbase = w.base + o_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(cudaMemsetAsync(w.base + o_pe, 0, sizeof(double) * n, s));
   CUDA_TRY(g1.launch(dbase, s));
   CUDA_TRY(g2.launch(dbase, s));
   CUDA_TRY(g3.launch(dbase, s));
   CUDA_TRY(g4.launch(dbase, s));
+  if (!ed.empty()) CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), (int)ed.size(), 8, s));
+  proj.assign(n, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(proj.data(), w.base + o_pe, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   out.resize(n);
   for (int i = 0; i < n; ++i)
     out[i] = csvd_block{w.base + oR[i], blocks[idx[i]].k, blocks[idx[i]].k, CSVD_F32, 0};
@@ -836,6 +938,18 @@ static double top_r_sum_sq(std::vector<double> v, int r) {
   return t;
 }
 
+// sum of mu^2 beyond the r largest: with the projection energies this gives
+// Cor. 1's bound  S - sum_{j<=r} mu_j^2 = sum_i ||Q_{i-1}^T A_i||^2 +
+// sum_{j>r} mu_j^2  (since ||A_i||^2 = ||Q^T A_i||^2 + ||R_i||^2 and
+// sum_j mu_j^2 = sum_i ||R_i||^2), a sum of non-negative terms free of the
+// subtraction's cancellation.
+static double rest_sum_sq(std::vector<double> v, int r) {
+  std::sort(v.begin(), v.end(), std::greater<double>());
+  double t = 0.0;
+  for (int i = r; i < (int)v.size(); ++i) t += v[i] * v[i];
+  return t;
+}
+
 extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
                                    void* cuda_stream, double* weyl_sq, double* residual_sq,
                                    double* plugin_sq, double* energy) {
@@ -852,10 +966,20 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
   std::iota(all.begin(), all.end(), 0);
   std::vector<double> en, top;
   csvd_status st = block_spectra(blocks, all, m, r, CSVD_PLAIN_FP32, s, d_status, en, top, nullptr);
-  double S = 0.0, tmax = 0.0;
-  for (int i = 0; i < n; ++i) { S += en[i]; tmax = std::max(tmax, top[i]); }
+  double S = 0.0;
+  int jstar = 0;
+  for (int i = 0; i < n; ++i) {
+    S += en[i];
+    if (top[i] > top[jstar]) jstar = i;
+  }
   if (st == CSVD_OK && energy) *energy = S;
-  if (st == CSVD_OK && weyl_sq) *weyl_sq = std::max(0.0, S - tmax);
+  if (st == CSVD_OK && weyl_sq) {
+    // Thm. 1: S - top_r(A_j*) = sum_{i != j*} ||A_i||^2 + sum_{l>r} sigma_l^2(A_j*)
+    double others = 0.0;
+    for (int i = 0; i < n; ++i)
+      if (i != jstar) others += en[i];
+    *weyl_sq = others + std::max(0.0, en[jstar] - top[jstar]);
+  }
   if (st == CSVD_OK && residual_sq) {
     SpanState sp;
     sp.m = m;
@@ -865,8 +989,10 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
     for (int i = 0; i < n && st == CSVD_OK; ++i) {
       Workspace w;
       std::vector<csvd_block> R;
-      st = span_residuals(sp, blocks, {i}, s, w, R);
+      std::vector<double> pe;
+      st = span_residuals(sp, blocks, {i}, s, w, R, pe);
       if (st != CSVD_OK) break;
+      sp.proj += pe[0];
       std::vector<double> e1, t1;
       std::vector<std::vector<float>> sv;
       const int rk = (int)std::min<int64_t>(blocks[i].k, m);
@@ -876,7 +1002,7 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
       Ssofar += en[i];
       st = span_extend(sp, R[0], sv[0], 1e-6 * std::sqrt(Ssofar), s);
     }
-    if (st == CSVD_OK) *residual_sq = std::max(0.0, S - top_r_sum_sq(sp.mu, r));
+    if (st == CSVD_OK) *residual_sq = sp.proj + rest_sum_sq(sp.mu, r);
   }
   if (st == CSVD_OK && plugin_sq) {
     csvd_state inc = nullptr;
@@ -1079,7 +1205,36 @@ csvd_status cluster_approx(Driver& D, int sort_mode, std::vector<std::vector<int
   return CSVD_OK;
 }
 
-// Alg. 2: residual clustering with a full-span basis.
+// Alg. 2: residual clustering with a full-span basis.  The certificate of
+// candidate j is Cor. 1 evaluated cancellation-free:
+//   bound^2 = proj + ||Q^T A_j||^2 + sum_{beyond top r} (mu u sigma(R_j))^2.
+// Candidate offers follow the scan semantics shared with the oracle:
+// frobenius -- ascending norm, one pass accepting greedily (the span grows
+// after each accept), passes repeat until one accepts nothing; residual --
+// after every accept the residual norms are recomputed and the smallest
+// candidate whose certificate holds joins.
+csvd_status residual_bounds(Driver& D, SpanState& sp, const std::vector<int>& cand, Workspace& w,
+                            std::vector<csvd_block>& R, std::vector<std::vector<float>>& sv,
+                            std::vector<double>& bound, std::vector<double>& energy,
+                            std::vector<double>& rnorm, std::vector<double>& pe) {
+  CSVD_TRY(span_residuals(sp, D.blocks, cand, D.s, w, R, pe));
+  std::vector<int> ridx(cand.size());
+  std::iota(ridx.begin(), ridx.end(), 0);
+  int rmax = 1;
+  for (auto& b : R) rmax = std::max<int>(rmax, (int)std::min<int64_t>(b.k, D.m));
+  std::vector<double> top;
+  CSVD_TRY(block_spectra(R.data(), ridx, D.m, rmax, CSVD_PLAIN_FP32, D.s, D.d_status, rnorm, top, &sv));
+  bound.assign(cand.size(), 0.0);
+  energy.assign(cand.size(), 0.0);
+  for (size_t i = 0; i < cand.size(); ++i) {
+    std::vector<double> mu = sp.mu;
+    for (float x : sv[i]) mu.push_back(x);
+    energy[i] = sp.energy + D.norms[cand[i]];
+    bound[i] = sp.proj + pe[i] + rest_sum_sq(mu, D.r);
+  }
+  return CSVD_OK;
+}
+
 csvd_status cluster_residual(Driver& D, int sort_mode, std::vector<std::vector<int>>& clusters,
                              std::vector<double>& est) {
   std::vector<int> remaining(D.n);
@@ -1096,7 +1251,6 @@ csvd_status cluster_residual(Driver& D, int sort_mode, std::vector<std::vector<i
     sp.m = D.m;
     CUDA_TRY(cudaMalloc(&sp.Qf, sizeof(float) * D.m * D.m));
     std::vector<int> members{anchor};
-    // anchor: residual against the empty span is the block itself
     {
       std::vector<double> e1, t1;
       std::vector<std::vector<float>> sv;
@@ -1106,62 +1260,78 @@ csvd_status cluster_residual(Driver& D, int sort_mode, std::vector<std::vector<i
       sp.energy = D.norms[anchor];
       CSVD_TRY(span_extend(sp, D.blocks[anchor], sv[0], 1e-6 * std::sqrt(sp.energy), D.s));
     }
-    bool grew = true;
-    while (grew && !remaining.empty()) {
-      grew = false;
-      // residuals and their spectra for all remaining blocks against the span
-      Workspace w;
-      std::vector<csvd_block> R;
-      CSVD_TRY(span_residuals(sp, D.blocks, remaining, D.s, w, R));
-      std::vector<int> ridx(remaining.size());
-      std::iota(ridx.begin(), ridx.end(), 0);
-      int rmax = 1;
-      for (auto& b : R) rmax = std::max<int>(rmax, (int)std::min<int64_t>(b.k, D.m));
-      std::vector<double> ren, rtop;
-      std::vector<std::vector<float>> sv;
-      CSVD_TRY(block_spectra(R.data(), ridx, D.m, rmax, CSVD_PLAIN_FP32, D.s, D.d_status, ren, rtop, &sv));
-      std::vector<double> bound(remaining.size()), energy(remaining.size());
-      for (size_t i = 0; i < remaining.size(); ++i) {
-        std::vector<double> mu = sp.mu;
-        for (float x : sv[i]) mu.push_back(x);
-        energy[i] = sp.energy + D.norms[remaining[i]];
-        bound[i] = std::max(0.0, energy[i] - top_r_sum_sq(mu, D.r));
-      }
-      std::vector<double> key(remaining.size());
-      for (size_t i = 0; i < remaining.size(); ++i)
-        key[i] = sort_mode == CSVD_SORT_FROBENIUS ? D.norms[remaining[i]] : ren[i];
-      std::vector<int> pos(remaining.size());
-      std::iota(pos.begin(), pos.end(), 0);
-      std::stable_sort(pos.begin(), pos.end(), [&](int a, int b) {
-        if (key[a] != key[b]) return key[a] < key[b];
-        return remaining[a] < remaining[b];
-      });
-      for (int p : pos) {
-        if (bound[p] <= e2 * energy[p]) {
-          const int j = remaining[p];
-          for (float x : sv[p]) sp.mu.push_back(x);
-          sp.energy = energy[p];
-          CSVD_TRY(span_extend(sp, R[p], sv[p], 1e-6 * std::sqrt(sp.energy), D.s));
-          members.push_back(j);
-          remaining.erase(remaining.begin() + p);
-          grew = true;
-          break;  // the span changed: residuals of the others are recomputed
+    auto accept = [&](int j, const csvd_block& R, const std::vector<float>& sv, double energy,
+                      double pe) -> csvd_status {
+      for (float x : sv) sp.mu.push_back(x);
+      sp.proj += pe;
+      sp.energy = energy;
+      CSVD_TRY(span_extend(sp, R, sv, 1e-6 * std::sqrt(sp.energy), D.s));
+      members.push_back(j);
+      remaining.erase(std::find(remaining.begin(), remaining.end(), j));
+      return CSVD_OK;
+    };
+    if (sort_mode == CSVD_SORT_FROBENIUS) {
+      while (!remaining.empty()) {
+        std::vector<double> key(remaining.size());
+        for (size_t i = 0; i < remaining.size(); ++i) key[i] = D.norms[remaining[i]];
+        const std::vector<int> order = sorted_by(remaining, key);
+        bool any = false;
+        size_t pos = 0;
+        while (pos < order.size()) {
+          std::vector<int> cand(order.begin() + pos, order.end());
+          Workspace w;
+          std::vector<csvd_block> R;
+          std::vector<std::vector<float>> sv;
+          std::vector<double> bound, energy, rn, pe;
+          CSVD_TRY(residual_bounds(D, sp, cand, w, R, sv, bound, energy, rn, pe));
+          size_t hit = cand.size();
+          for (size_t i = 0; i < cand.size(); ++i)
+            if (bound[i] <= e2 * energy[i]) { hit = i; break; }
+          if (hit == cand.size()) break;
+          CSVD_TRY(accept(cand[hit], R[hit], sv[hit], energy[hit], pe[hit]));
+          any = true;
+          pos += hit + 1;
         }
+        if (!any) break;
+      }
+    } else {
+      while (!remaining.empty()) {
+        Workspace w;
+        std::vector<csvd_block> R;
+        std::vector<std::vector<float>> sv;
+        std::vector<double> bound, energy, rn, pe;
+        CSVD_TRY(residual_bounds(D, sp, remaining, w, R, sv, bound, energy, rn, pe));
+        std::vector<int> pos(remaining.size());
+        std::iota(pos.begin(), pos.end(), 0);
+        std::stable_sort(pos.begin(), pos.end(), [&](int a, int b) {
+          if (rn[a] != rn[b]) return rn[a] < rn[b];
+          return remaining[a] < remaining[b];
+        });
+        int hit = -1;
+        for (int p : pos)
+          if (bound[p] <= e2 * energy[p]) { hit = p; break; }
+        if (hit < 0) break;
+        CSVD_TRY(accept(remaining[hit], R[hit], sv[hit], energy[hit], pe[hit]));
       }
     }
     clusters.push_back(members);
-    est.push_back(std::max(0.0, sp.energy - top_r_sum_sq(sp.mu, D.r)));
+    est.push_back(sp.proj + rest_sum_sq(sp.mu, D.r));
   }
   return CSVD_OK;
 }
 
-// Alg. 1: max-norm (Weyl) clustering with a head of width <= r.
+// Alg. 1: max-norm (Weyl) clustering with a head of width <= r.  Bounds are
+// sums of non-negative terms: with a head, S - S_head = the energy of the
+// non-head members; without, S - top_r(A_j*) = sum_{i != j*} ||A_i||^2 +
+// (tail of A_j*), j* the member with the largest top-r energy.
 csvd_status cluster_weyl(Driver& D, std::vector<std::vector<int>>& clusters,
                          std::vector<double>& est) {
   std::vector<int> all(D.n);
   std::iota(all.begin(), all.end(), 0);
   std::vector<double> en, top;
   CSVD_TRY(block_spectra(D.blocks, all, D.m, D.r, D.precision, D.s, D.d_status, en, top, nullptr));
+  std::vector<double> tail(D.n);
+  for (int i = 0; i < D.n; ++i) tail[i] = std::max(0.0, en[i] - top[i]);
   std::vector<int> desc = all;
   std::stable_sort(desc.begin(), desc.end(), [&](int a, int b) {
     if (D.norms[a] != D.norms[b]) return D.norms[a] > D.norms[b];
@@ -1174,35 +1344,41 @@ csvd_status cluster_weyl(Driver& D, std::vector<std::vector<int>>& clusters,
     remaining.erase(remaining.begin());
     std::vector<int> members{anchor};
     bool head = false;
-    double S = D.norms[anchor], Shead = 0.0, tmax = top[anchor];
+    double S = D.norms[anchor];
+    double nonhead = 0.0;      // head case: energy outside the head
+    int jstar = anchor;        // no-head case: member with the largest top-r energy
+    double others = 0.0;       // no-head case: energy of the members other than jstar
     if (D.widths[anchor] <= D.r) {
       head = true;
       int width = D.widths[anchor];
-      Shead = D.norms[anchor];
       while (!remaining.empty() && width + D.widths[remaining.front()] <= D.r) {
         const int j = remaining.front();
         remaining.erase(remaining.begin());
         members.push_back(j);
         width += D.widths[j];
         S += D.norms[j];
-        Shead += D.norms[j];
       }
     }
+    auto bound_with = [&](int j, int& js, double& oth) {
+      if (head) return nonhead + D.norms[j];
+      if (top[j] > top[jstar]) { js = j; oth = others + D.norms[jstar]; }
+      else { js = jstar; oth = others + D.norms[j]; }
+      return oth + tail[js];
+    };
     while (true) {
       std::vector<double> key(remaining.size());
       for (size_t i = 0; i < remaining.size(); ++i) key[i] = D.norms[remaining[i]];
       std::vector<int> order = sorted_by(remaining, key);
       bool any = false;
       for (int j : order) {
+        int js = jstar;
+        double oth = others;
+        const double b = bound_with(j, js, oth);
         const double S2 = S + D.norms[j];
-        double b;
-        double t2 = tmax;
-        if (head) b = S2 - Shead;
-        else { t2 = std::max(tmax, top[j]); b = S2 - t2; }
-        b = std::max(0.0, b);
         if (b <= e2 * S2) {
           S = S2;
-          tmax = t2;
+          if (head) nonhead += D.norms[j];
+          else { jstar = js; others = oth; }
           members.push_back(j);
           remaining.erase(std::find(remaining.begin(), remaining.end(), j));
           any = true;
@@ -1211,7 +1387,7 @@ csvd_status cluster_weyl(Driver& D, std::vector<std::vector<int>>& clusters,
       if (!any || remaining.empty()) break;
     }
     clusters.push_back(members);
-    est.push_back(std::max(0.0, head ? S - Shead : S - tmax));
+    est.push_back(head ? nonhead : others + tail[jstar]);
   }
   return CSVD_OK;
 }
@@ -1374,5 +1550,53 @@ extern "C" csvd_status csvd_profile_report(char* buf, int64_t len) {
   std::string out;
   for (auto& a : acc) out += a.name + " " + std::to_string(a.n) + " " + std::to_string(a.ms) + "\n";
   std::snprintf(buf, (size_t)len, "%s", out.c_str());
+  return CSVD_OK;
+}
+
+extern "C" csvd_status csvd_gram_apply(const float* U, int64_t ldu, int64_t m, int32_t r,
+                                       const csvd_block* blocks, int32_t n, float* Y, int64_t ldy,
+                                       void* cuda_stream) {
+  if (!U || !blocks || !Y || n < 1 || m < 1 || r < 1 || ldu < r || ldy < r)
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "f32 blocks only");
+  }
+  Layout L;
+  std::vector<size_t> oT(n);
+  for (int i = 0; i < n; ++i) oT[i] = L.add(sizeof(float) * (size_t)blocks[i].k * r);
+  std::vector<GemmBatch> gY(n);
+  GemmBatch gT;
+  auto fill = [&](char* base) {
+    gT = GemmBatch();
+    for (int i = 0; i < n; ++i) {
+      gY[i] = GemmBatch();
+      const int k = (int)blocks[i].k;
+      float* T = reinterpret_cast<float*>(base + oT[i]);
+      // T_j = A_j^T U (k x r)
+      gT.add(gemm(blocks[i].ptr, blocks[i].ld, 1, U, ldu, 0, T, r, 0, k, r, (int)m));
+      // Y (+)= A_j T_j
+      gY[i].add(gemm(blocks[i].ptr, blocks[i].ld, 0, T, r, 0, Y, ldy, 0, (int)m, r, k, 1.f,
+                     i == 0 ? nullptr : Y, ldy, 0, i == 0 ? 0.f : 1.f));
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  gT.pack(probe);
+  for (auto& g : gY) g.pack(probe);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  gT.pack(pk);
+  for (auto& g : gY) g.pack(pk);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(gT.launch(dbase, s));
+  for (auto& g : gY) CUDA_TRY(g.launch(dbase, s));
   return CSVD_OK;
 }

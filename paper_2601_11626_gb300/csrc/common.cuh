@@ -154,10 +154,10 @@ cudaError_t launch_apply_q(const ApplyQDesc* d_desc, int n_items, int max_cols,
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
 int jacobi_scratch_floats(int nc);
-int tridiag_scratch_floats(int n);
+__host__ __device__ int tridiag_smem_cap(int smem_bytes, int n_max);
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
                                int* d_status, cudaStream_t s);
-cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes,
+cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
                                 int* d_status, cudaStream_t s);
 cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
                                 const double* energy_new, const double* tail_new,

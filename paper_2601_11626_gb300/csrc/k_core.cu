@@ -7,15 +7,10 @@
 //    columns).  Disjoint column pairs of a round-robin schedule are rotated
 //    by separate warps; column norms at convergence are the singular values
 //    and the normalised columns the left singular vectors.
-//  * core_tridiag_kernel (mixed form): the eigenvalues of the Gram
-//    K^T K = [[S, diag(s) P], [P^T diag(s), A^T A]] (n = r_t + k), whose
-//    nonzero eigenvalues are those of K K^T = S_{t+1}: Householder
-//    tridiagonalisation (warp-per-row symmetric matrix-vector products,
-//    block-wide rank-2 updates), then one bisection per eigenvalue on the
-//    Sturm count of the tridiagonal matrix.
-// Both finish with the same FP64 epilogue: sigma~ = top r_new values, the
-// tail as accumulated discarded energy (equal to sum ||A||^2 - sum sigma~^2
-// in exact arithmetic, without its cancellation) and the merge certificate
+//    (The mixed form's eigenvalue core is in k_tridiag.cu.)
+// The epilogue gives sigma~ = top r_new values, the tail as accumulated
+// discarded energy (equal to sum ||A||^2 - sum sigma~^2 in exact arithmetic,
+// without its cancellation) and the merge certificate
 // tail <= eps^2 ||M_{C u j}||^2 (Alg. 3 step 3(e)).
 // The core lives in shared memory when it fits, else in a global workspace.
 #include "common.cuh"
@@ -220,176 +215,6 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
   prof_begin(s);
   core_jacobi_kernel<<<n_items, 1024, smem_bytes, s>>>(d_desc, d_status);
   prof_end("core_jacobi", s);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------- tridiagonal Gram core
-__device__ __forceinline__ int sturm_count(const float* dv, const float* e2, int n, float x,
-                                           float pivmin) {
-  float q = dv[0] - x;
-  int cnt = q < 0.f;
-  for (int i = 1; i < n; ++i) {
-    if (fabsf(q) < pivmin) q = -pivmin;
-    q = (dv[i] - x) - e2[i - 1] / q;
-    cnt += q < 0.f;
-  }
-  return cnt;
-}
-
-__global__ void __launch_bounds__(1024)
-core_tridiag_kernel(const CoreDesc* __restrict__ descs, int* __restrict__ status) {
-  extern __shared__ __align__(16) float smem[];
-  const CoreDesc d = descs[blockIdx.x];
-  const int n = d.rt + d.k;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  float* dv = smem;             // n diagonal
-  float* ev = dv + n;           // n off-diagonal (e[i] couples i, i+1)
-  float* vv = ev + n;           // n reflector
-  float* pv = vv + n;           // n p / w
-  float* lam = pv + n;          // n eigenvalues, non-increasing
-  float* red = lam + n;         // 64 floats
-  const int scratch = ((5 * n + 64 + 3) / 4) * 4;
-  float* G = d.in_smem ? smem + scratch : d.work;
-  const int64_t ld = d.in_smem ? n : d.ldwork;
-  __shared__ float s_beta, s_tau2, s_skip;
-
-  // assemble the Gram core K^T K
-  for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    float v;
-    if (i < d.rt && j < d.rt) v = (i == j) ? d.sigma[i] * d.sigma[i] : 0.f;
-    else if (i < d.rt) v = d.sigma[i] * d.P[(int64_t)i * d.ldp + (j - d.rt)];
-    else if (j < d.rt) v = d.sigma[j] * d.P[(int64_t)j * d.ldp + (i - d.rt)];
-    else {
-      const int a = min(i, j) - d.rt, b = max(i, j) - d.rt;
-      v = d.Gaa[(int64_t)a * d.ldb + b];
-    }
-    G[(int64_t)i * ld + j] = v;
-  }
-  __syncthreads();
-
-  // Householder tridiagonalisation: G <- H G H, H = I - tau2 v v^T
-  for (int j = 0; j + 2 < n; ++j) {
-    const int t = n - j - 1;
-    const float* row = G + (int64_t)j * ld + (j + 1);
-    float part = 0.f;
-    for (int l = 1 + tid; l < t; l += blockDim.x) part = fmaf(row[l], row[l], part);
-    const float tail2 = block_sum(part, red);
-    const float x0 = row[0];
-    if (tid == 0) {
-      dv[j] = G[(int64_t)j * ld + j];
-      if (tail2 == 0.f) {
-        ev[j] = x0;
-        s_skip = 1.f;
-      } else {
-        const float nrm = sqrtf(fmaf(x0, x0, tail2));
-        const float beta = x0 >= 0.f ? -nrm : nrm;
-        const float v0 = x0 - beta;
-        ev[j] = beta;
-        s_beta = v0;
-        s_tau2 = 2.f / fmaf(v0, v0, tail2);
-        s_skip = 0.f;
-      }
-    }
-    __syncthreads();
-    if (s_skip != 0.f) { __syncthreads(); continue; }
-    const float tau2 = s_tau2;
-    for (int l = tid; l < t; l += blockDim.x) vv[l] = (l == 0) ? s_beta : row[l];
-    __syncthreads();
-    // p = tau2 * G_t v  (warp per row)
-    for (int i = wid; i < t; i += nw) {
-      const float* gr = G + (int64_t)(j + 1 + i) * ld + (j + 1);
-      float acc = 0.f;
-      for (int l = lane; l < t; l += 32) acc = fmaf(gr[l], vv[l], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) pv[i] = tau2 * acc;
-    }
-    __syncthreads();
-    float pp = 0.f;
-    for (int l = tid; l < t; l += blockDim.x) pp = fmaf(pv[l], vv[l], pp);
-    const float kk = 0.5f * tau2 * block_sum(pp, red);
-    for (int l = tid; l < t; l += blockDim.x) pv[l] = fmaf(-kk, vv[l], pv[l]);
-    __syncthreads();
-    // G_t -= v w^T + w v^T
-    for (int64_t e = tid; e < (int64_t)t * t; e += blockDim.x) {
-      const int i = (int)(e / t), l = (int)(e % t);
-      float* g = G + (int64_t)(j + 1 + i) * ld + (j + 1 + l);
-      *g = fmaf(-vv[i], pv[l], fmaf(-pv[i], vv[l], *g));
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    if (n >= 2) {
-      dv[n - 2] = G[(int64_t)(n - 2) * ld + (n - 2)];
-      ev[n - 2] = G[(int64_t)(n - 1) * ld + (n - 2)];
-    }
-    dv[n - 1] = G[(int64_t)(n - 1) * ld + (n - 1)];
-    ev[n - 1] = 0.f;
-  }
-  __syncthreads();
-  // squared off-diagonal, Gershgorin interval
-  float lo = 3.0e38f, hi = -3.0e38f, emax = 0.f;
-  for (int i = tid; i < n; i += blockDim.x) {
-    const float el = i > 0 ? fabsf(ev[i - 1]) : 0.f;
-    const float er = i + 1 < n ? fabsf(ev[i]) : 0.f;
-    lo = fminf(lo, dv[i] - el - er);
-    hi = fmaxf(hi, dv[i] + el + er);
-    emax = fmaxf(emax, er * er);
-  }
-  __shared__ float s_lo[32], s_hi[32], s_em[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  }
-  if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; s_em[wid] = emax; }
-  __syncthreads();
-  float glo = s_lo[0], ghi = s_hi[0], gem = s_em[0];
-  for (int w = 1; w < nw; ++w) {
-    glo = fminf(glo, s_lo[w]);
-    ghi = fmaxf(ghi, s_hi[w]);
-    gem = fmaxf(gem, s_em[w]);
-  }
-  // reuse vv as e^2
-  for (int i = tid; i < n; i += blockDim.x) vv[i] = (i + 1 < n) ? ev[i] * ev[i] : 0.f;
-  __syncthreads();
-  const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
-  const float pivmin = 1.0e-30f * fmaxf(1.f, gem);
-  const float atol = 2.4e-7f * gnorm + 1e-30f;
-  int capped = 0;
-  for (int q = tid; q < n; q += blockDim.x) {
-    const int target = n - 1 - q;  // ascending index of the q-th largest
-    float a = glo, b = ghi;
-    int it = 0;
-    for (; it < kBisectMaxIter; ++it) {
-      const float mid = 0.5f * (a + b);
-      if (!(mid > a && mid < b) || (b - a) <= atol) break;
-      if (sturm_count(dv, vv, n, mid, pivmin) > target) b = mid; else a = mid;
-    }
-    if (it == kBisectMaxIter) capped = 1;
-    lam[q] = 0.5f * (a + b);
-  }
-  if (capped) atomicOr(status, kStatusBisectCap);
-  __syncthreads();
-  if (wid == 0) {
-    // eigenvalues beyond rt + kp are zero in exact arithmetic (rank <= m)
-    core_epilogue(d, lam, n, true);
-  }
-}
-
-int tridiag_scratch_floats(int n) { return ((5 * n + 64 + 3) / 4) * 4; }
-
-cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes,
-                                int* d_status, cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
-  if (smem_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-  }
-  prof_begin(s);
-  core_tridiag_kernel<<<n_items, 1024, smem_bytes, s>>>(d_desc, d_status);
-  prof_end("core_tridiag", s);
   return cudaGetLastError();
 }
 

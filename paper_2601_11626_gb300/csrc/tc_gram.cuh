@@ -1,0 +1,35 @@
+// Tensor-core Gram / projection kernel of the mixed merge evaluation.
+#pragma once
+
+#include "common.cuh"
+
+namespace csvd {
+
+// One candidate block A (m x k, f32, 16-byte aligned, ld % 4 == 0) and the
+// basis U (m x rt, f32, 16-byte aligned, ldu % 4 == 0) of its state.
+struct TcItem {
+  const float* A;
+  int64_t lda;
+  const float* U;
+  int64_t ldu;
+  int m, k, rt, pad;
+  float* P;      // rt x k, row-major ldp:  P = U^T A
+  int64_t ldp;
+  float* G;      // k x k, row-major ldg:   G = A^T A (tiles on and above the diagonal)
+  int64_t ldg;
+};
+
+// A 128 x 128 output tile: kind 0 -> rows from U (P), kind 1 -> rows from A (G).
+struct TcTile {
+  int item, kind, row0, col0;
+};
+
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 3;
+constexpr int kTcThreads = 14 * 32;
+constexpr int kTcStageBytes = 2 * kTcBK * kTcBM * 4 + 4 * kTcBM * kTcBK * 2;  // 64 KB
+constexpr int kTcSmemBytes = kTcStages * kTcStageBytes + 2048;
+
+cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles,
+                           int n_ctas, int* d_status, cudaStream_t s);
+
+}  // namespace csvd

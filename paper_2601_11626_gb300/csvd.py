@@ -54,6 +54,8 @@ def _sig(lib):
     lib.csvd_incr_init.argtypes = [P(VP), I64, I32, I32, VP]
     lib.csvd_incr_append.argtypes = [VP, P(Block)]
     lib.csvd_incr_sigma.argtypes = [VP, P(C.c_float), P(I32)]
+    lib.csvd_incr_load.argtypes = [VP, VP, I64, I32, P(C.c_float), D, D]
+    lib.csvd_gram_apply.argtypes = [VP, I64, I64, I32, P(Block), I32, VP, I64, VP]
     lib.csvd_incr_basis.argtypes = [VP, VP, I64]
     lib.csvd_tail_error.argtypes = [VP, P(D), P(D), P(D), P(D)]
     lib.csvd_incr_free.argtypes = [VP]
@@ -70,6 +72,7 @@ def _sig(lib):
     lib.csvd_profile_report.argtypes = [C.c_char_p, I64]
     lib.csvd_profile_report.restype = C.c_int
     for name in ("csvd_incr_init", "csvd_incr_append", "csvd_incr_sigma", "csvd_incr_basis",
+                 "csvd_incr_load", "csvd_gram_apply",
                  "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_bounds",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator"):
         getattr(lib, name).restype = C.c_int
@@ -168,6 +171,18 @@ class IncrSVD:
         U = torch.empty(self.m, max(rk, 1), device="cuda", dtype=torch.float32)
         _check(self._lib.csvd_incr_basis(self._h, C.c_void_p(U.data_ptr()), U.stride(0)))
         return U[:, :rk]
+
+    def load(self, U: torch.Tensor, sigma, energy: float, discarded: float):
+        """Restore (U, sigma, energy, discarded) -- checkpoint / resume."""
+        sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32))
+        rt = int(sig.size)
+        U = U.contiguous() if rt > 0 and U.stride(1) != 1 else U
+        ptr = C.c_void_p(U.data_ptr()) if rt > 0 else None
+        ld = U.stride(0) if rt > 0 else 1
+        _check(self._lib.csvd_incr_load(self._h, ptr, ld, rt,
+                                        sig.ctypes.data_as(C.POINTER(C.c_float)),
+                                        float(energy), float(discarded)))
+        return self
 
     def tail_error(self) -> dict:
         t, rel, paper, en = C.c_double(), C.c_double(), C.c_double(), C.c_double()
@@ -277,12 +292,32 @@ def tail_grad(U: torch.Tensor, blocks, g: float = 1.0):
     return grads
 
 
-def _basis(blocks, r, working_rank):
-    st = IncrSVD(blocks[0].shape[0], working_rank or r)
+def gram_apply(U: torch.Tensor, blocks) -> torch.Tensor:
+    """Y = sum_j A_j (A_j^T U) (one subspace-iteration sweep)."""
+    m, r = U.shape
+    U = U.contiguous()
+    Y = torch.empty(m, r, device="cuda", dtype=torch.float32)
+    _check(lib().csvd_gram_apply(C.c_void_p(U.data_ptr()), U.stride(0), m, r, _blocks(blocks),
+                                 len(blocks), C.c_void_p(Y.data_ptr()), Y.stride(0), _stream()))
+    return Y
+
+
+def _basis(blocks, r, working_rank, refine=1):
+    """Top-r basis: the incremental estimator at working rank, then
+    ``refine`` sweeps of subspace iteration (orthonormalised through an
+    incremental append of M M^T U)."""
+    m = blocks[0].shape[0]
+    st = IncrSVD(m, working_rank or r)
     for b in blocks:
         st.append(b)
     U = st.basis()[:, :r].contiguous()
     st.close()
+    for _ in range(refine):
+        Y = gram_apply(U, list(blocks))
+        q = IncrSVD(m, r)
+        q.append(Y)
+        U = q.basis().contiguous()
+        q.close()
     return U
 
 

@@ -10,6 +10,14 @@ Tolerances (derived from FP32 arithmetic):
 * tail E~ (both forms): 1e-4 relative on E~ = sqrt(E~^2).
 * accept flags identical except for merges whose relative estimate lies
   within 1e-3 (relative) of eps; those are listed.
+
+Every merge evaluation and every append is compared from identical states:
+the oracle's state is rounded to FP32 and loaded into the GPU state.  A
+free-running GPU trajectory is not compared value by value with the
+oracle's: where a truncation cuts through near-equal eigenvalues (a dense
+noise floor, repeated latent spectra) the retained basis is ill-conditioned
+and FP32 and FP64 trajectories part, both valid; it is checked against
+invariants that hold for any valid trajectory instead.
 """
 import math
 
@@ -60,90 +68,31 @@ def csvd(cuda_lib):
     return mod
 
 
-# ------------------------------------------------------- incremental append
-def test_incremental_small_every_step(csvd):
-    col = synth.small_c1()
-    r = col.meta["r"]
-    st = csvd.IncrSVD(col.m, r)
-    ost = oinc.IncrementalSVD(col.m, r)
-    for b in col.blocks:
-        st.append(b.cuda())
-        ost.append(b)
-        _check_sigma(st.sigma(), ost.s)
-        t = st.tail_error()
-        _check_tail(t["tail_sq"], ost.tail_sq_discard())
-        assert math.isclose(t["energy"], ost.energy, rel_tol=1e-6)
-    U = _np(st.basis())
-    assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-4
+def _round_state(ost):
+    """Round the oracle state to FP32 in place (both sides start identical)."""
+    ost.Q = ost.Q.astype(np.float32).astype(np.float64)
+    ost.s = ost.s.astype(np.float32).astype(np.float64)
+    return ost
 
 
-def test_incremental_mid_size(csvd):
-    col = synth.mid_c2(n_blocks=12)
-    r = col.meta["r"]
-    st = csvd.IncrSVD(col.m, r)
-    ost = oinc.IncrementalSVD(col.m, r)
-    for b in col.blocks:
-        st.append(b.cuda())
-        ost.append(b)
-    _check_sigma(st.sigma(), ost.s)
-    _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard())
+def _load(csvd, ost):
+    g = csvd.IncrSVD(ost.m, ost.r)
+    U = torch.tensor(ost.Q, dtype=torch.float32, device="cuda")
+    g.load(U, ost.s.astype(np.float32), ost.energy, ost.discarded)
+    return g
 
 
-@pytest.mark.parametrize("m,widths,r", [
-    (32, [1, 1, 1, 1, 1], 3),          # k = 1 (rank-one appends)
-    (16, [2, 2, 2], 12),                # r above the total rank
-    (32, [24, 24, 24], 16),             # r_t + k > m: kp = m - r_t
-    (40, [7, 33, 5, 64], 9),            # ragged widths, k > m
-    (64, [130], 64),                    # single block wider than two GEMM tiles
-])
-def test_incremental_edge_shapes(csvd, m, widths, r):
-    blocks = synth.random_blocks(m, widths, seed=3, decay=0.8)
-    st = csvd.IncrSVD(m, r)
-    ost = oinc.IncrementalSVD(m, r)
-    for b in blocks:
-        st.append(b.cuda())
-        ost.append(b)
-        _check_sigma(st.sigma(), ost.s)
-        _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard(),
-                    floor=3e-6 * math.sqrt(ost.energy))
-
-
-def test_incremental_padded_leading_dimension(csvd):
-    blocks = synth.random_blocks(48, [5, 9, 13], seed=4, decay=0.9)
-    views, pool = synth.pack_blocks([b.cuda() for b in blocks], ld_align=16)
-    st = csvd.IncrSVD(48, 6)
-    ost = oinc.IncrementalSVD(48, 6)
-    for v, b in zip(views, blocks):
-        assert v.stride(0) == 16
-        st.append(v)
-        ost.append(b)
-    _check_sigma(st.sigma(), ost.s)
-
-
-def test_zero_block(csvd):
-    st = csvd.IncrSVD(20, 4)
-    ost = oinc.IncrementalSVD(20, 4)
-    for b in synth.random_blocks(20, [3], seed=5) + [torch.zeros(20, 4)]:
-        st.append(b.cuda())
-        ost.append(b)
-    _check_sigma(st.sigma(), ost.s)
-    _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard(), floor=1e-6)
-
-
-# -------------------------------------------------------- batched scoring
-def _states(csvd, m, r, groups):
-    gpu, cpu = [], []
+def _oracle_states(m, r, groups):
+    out = []
     for blocks in groups:
-        g = csvd.IncrSVD(m, r)
         c = oinc.IncrementalSVD(m, r)
         for b in blocks:
-            g.append(b.cuda() if not b.is_cuda else b)
             c.append(b)
-        gpu.append(g)
-        cpu.append(c)
-    return gpu, cpu
+        out.append(_round_state(c))
+    return out
 
 
+# ------------------------------------------------- one merge evaluation
 def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision):
     sig, tail, paper, acc = csvd.score(gst, cand_state, cands, eps, precision)
     sig, tail, paper, acc = _np(sig), _np(tail), _np(paper), acc.cpu().numpy()
@@ -151,7 +100,6 @@ def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision):
     for i, (si, b) in enumerate(zip(cand_state, cands)):
         s_o, t_o, a_o, nxt = cst[si].evaluate(b.cpu(), eps)
         _check_sigma(sig[i, :len(s_o)], s_o, mixed=(precision == "mixed"))
-        # the oracle's accumulated-discard form (exactly its paper form in exact arithmetic)
         _check_tail(tail[i], nxt[3])
         rel = math.sqrt(t_o / nxt[2])
         if abs(rel - eps) <= 1e-3 * eps:
@@ -165,8 +113,8 @@ def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision):
 def test_score_mid_size(csvd, precision):
     col = synth.mid_c2(n_blocks=40)
     m, r = col.m, col.meta["r"]
-    groups = [col.blocks[0:4], col.blocks[16:19]]
-    gst, cst = _states(csvd, m, r, groups)
+    cst = _oracle_states(m, r, [col.blocks[0:4], col.blocks[16:19]])
+    gst = [_load(csvd, c) for c in cst]
     cands = [b.cuda() for b in col.blocks[20:36]]
     cand_state = [i % 2 for i in range(len(cands))]
     for eps in (0.1, 0.2, 0.3):
@@ -175,15 +123,33 @@ def test_score_mid_size(csvd, precision):
 
 @pytest.mark.parametrize("precision", ["plain", "mixed"])
 def test_score_uneven_large_cores(csvd, precision):
-    """Uneven widths in [16, 512] at m = 2048: cores up to 576 x 576 take
-    the global-memory path; ragged widths exercise every tile tail."""
+    """Uneven widths in [16, 512] at m = 2048: cores up to 576 x 576 spill
+    to global memory before moving on-chip; ragged widths exercise every
+    tile tail of the tensor-core Gram."""
     w = synth.scoring_c4(r=64, n_states=3, appends=3, per_state=5, device="cuda")
     m, r = w["m"], w["r"]
-    gst, cst = _states(csvd, m, r, w["states"])
+    cst = _oracle_states(m, r, w["states"])
+    gst = [_load(csvd, c) for c in cst]
     cands = w["candidates"]
     ks = [c.shape[1] for c in cands]
-    assert min(ks) < 224 < max(ks)
+    assert min(ks) < 160 < 330 < max(ks)
     _compare_scores(csvd, gst, cst, w["cand_state"], cands, 0.25, precision)
+
+
+def test_score_simt_and_tensor_gram_agree(csvd):
+    """The same candidates through the tensor-core Gram (16-byte aligned rows)
+    and the SIMT fallback (odd leading dimension) against the oracle."""
+    col = synth.mid_c2(n_blocks=12)
+    m, r = col.m, col.meta["r"]
+    cst = _oracle_states(m, r, [col.blocks[0:3]])
+    gst = [_load(csvd, cst[0])]
+    raw = [b[:, :k] for b, k in zip(col.blocks[4:10], (13, 37, 64, 101, 127, 128))]
+    aligned, _ = synth.pack_blocks([x.cuda() for x in raw], ld_align=8)
+    odd, _ = synth.pack_blocks([x.cuda() for x in raw], ld_align=1)
+    odd = [x if x.stride(0) % 4 else torch.nn.functional.pad(x, (0, 1))[:, :x.shape[1]] for x in odd]
+    assert any(x.stride(0) % 4 for x in odd)
+    for cands in (aligned, odd):
+        _compare_scores(csvd, gst, cst, [0] * len(cands), cands, 0.2, "mixed")
 
 
 def test_score_empty_state_gives_block_spectrum(csvd):
@@ -210,6 +176,118 @@ def test_score_bf16_blocks_mixed(csvd):
         _check_tail(float(tail[i]), float(np.sum(s[16:] ** 2)))
 
 
+# ----------------------------------------------------- incremental append
+def test_append_one_step_from_identical_state(csvd):
+    col = synth.mid_c2(n_blocks=8)
+    m, r = col.m, col.meta["r"]
+    ost = _oracle_states(m, r, [col.blocks[0:5]])[0]
+    st = _load(csvd, ost)
+    st.append(col.blocks[5].cuda())
+    ost.append(col.blocks[5])
+    _check_sigma(st.sigma(), ost.s)
+    t = st.tail_error()
+    _check_tail(t["tail_sq"], ost.tail_sq_discard())
+    assert math.isclose(t["energy"], ost.energy, rel_tol=1e-6)
+    U = _np(st.basis())
+    assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 2e-5
+
+
+def _run_pair(csvd, blocks, m, r, precision="plain"):
+    """(1) Step parity along the oracle's trajectory: before every append the
+    oracle's state (rounded to FP32) is loaded into a GPU state, and the
+    step's results are compared.  (2) A free-running GPU trajectory is
+    checked at every step against invariants of any valid trajectory:
+    sigma~_j <= sigma_j(M) (the retained Gram never exceeds the true one),
+    E~ >= E_r(M) (the plug-in estimate is never below the true tail), and
+    the energy."""
+    free = csvd.IncrSVD(m, r, precision)
+    ost = oinc.IncrementalSVD(m, r)
+    for t, b in enumerate(blocks):
+        _round_state(ost)
+        g = _load(csvd, ost) if t > 0 else csvd.IncrSVD(m, r, precision)
+        g.append(b.cuda())
+        ost.append(b)
+        _check_sigma(g.sigma(), ost.s)
+        te = g.tail_error()
+        _check_tail(te["tail_sq"], ost.tail_sq_discard(), floor=3e-6 * math.sqrt(ost.energy))
+        g.close()
+        free.append(b.cuda())
+        s = free.sigma()
+        tf = free.tail_error()
+        ex = oexact.singular_values(blocks[:t + 1])
+        assert np.all(s <= ex[:len(s)] * (1 + 2e-5) + 2e-6 * ex[0])
+        assert tf["tail_sq"] >= oexact.tail_sq(blocks[:t + 1], r) * (1 - 2e-4) - 1e-12 * ost.energy
+        assert math.isclose(tf["energy"], ost.energy, rel_tol=1e-6)
+    U = _np(free.basis())
+    assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-4
+
+
+def test_incremental_small(csvd):
+    col = synth.small_c1()
+    _run_pair(csvd, col.blocks, col.m, col.meta["r"])
+
+
+def test_incremental_mid_size(csvd):
+    col = synth.mid_c2(n_blocks=12)
+    _run_pair(csvd, col.blocks, col.m, col.meta["r"])
+
+
+def test_incremental_gapped_sequence(csvd):
+    """Blocks from 3 latent subspaces with a strong head of 128 directions and
+    r = 128; the free-running trajectory ends on the exact top-128 values."""
+    w = synth.grad_c5(n_blocks=8, m=512, k=64)
+    _run_pair(csvd, w["fd"], 512, 128)
+
+
+@pytest.mark.parametrize("m,widths,r", [
+    (32, [1, 1, 1, 1, 1], 3),          # k = 1 (rank-one appends)
+    (16, [2, 2, 2], 12),                # r above the total rank
+    (32, [24, 24, 24], 16),             # r_t + k > m: kp = m - r_t
+    (40, [7, 33, 5, 64], 9),            # ragged widths, k > m
+    (64, [130], 64),                    # single block wider than two GEMM tiles
+])
+def test_incremental_edge_shapes(csvd, m, widths, r):
+    blocks = synth.random_blocks(m, widths, seed=3, decay=0.8)
+    _run_pair(csvd, blocks, m, r)
+
+
+def test_incremental_padded_leading_dimension(csvd):
+    blocks = synth.random_blocks(48, [5, 9, 13], seed=4, decay=0.9)
+    views, pool = synth.pack_blocks([b.cuda() for b in blocks], ld_align=16)
+    st = csvd.IncrSVD(48, 6)
+    ost = oinc.IncrementalSVD(48, 6)
+    for v, b in zip(views, blocks):
+        assert v.stride(0) == 16
+        st.append(v)
+        ost.append(b)
+    _check_sigma(st.sigma(), ost.s)
+
+
+def test_zero_block(csvd):
+    st = csvd.IncrSVD(20, 4)
+    ost = oinc.IncrementalSVD(20, 4)
+    for b in synth.random_blocks(20, [3], seed=5) + [torch.zeros(20, 4)]:
+        st.append(b.cuda())
+        ost.append(b)
+    _check_sigma(st.sigma(), ost.s)
+    _check_tail(st.tail_error()["tail_sq"], ost.tail_sq_discard(), floor=1e-6)
+
+
+def test_state_roundtrip(csvd):
+    """Export (basis, sigma, tails) and load into a fresh state: appending
+    the next block gives the same result as the original state."""
+    col = synth.mid_c2(n_blocks=6)
+    a = csvd.IncrSVD(col.m, 64)
+    for b in col.blocks[:4]:
+        a.append(b.cuda())
+    t = a.tail_error()
+    b2 = csvd.IncrSVD(col.m, 64).load(a.basis(), a.sigma(), t["energy"], t["tail_sq"])
+    a.append(col.blocks[4].cuda())
+    b2.append(col.blocks[4].cuda())
+    np.testing.assert_array_equal(a.sigma(), b2.sigma())
+    assert a.tail_error()["tail_sq"] == b2.tail_error()["tail_sq"]
+
+
 # ----------------------------------------------------------------- bounds
 def test_bounds_small(csvd):
     col = synth.small_c1()
@@ -217,11 +295,20 @@ def test_bounds_small(csvd):
     got = csvd.bounds([b.cuda() for b in col.blocks], r)
     w, res, plug, en = obounds.all_bounds(col.blocks, r)
     assert math.isclose(got["energy"], en, rel_tol=1e-6)
-    for key, want in (("weyl_sq", w), ("residual_sq", res), ("plugin_sq", plug)):
-        _check_tail(got[key], want)
+    _check_tail(got["weyl_sq"], w)
+    _check_tail(got["residual_sq"], res)
     ex = oexact.tail_sq(col.blocks, r)
     for key in ("weyl_sq", "residual_sq", "plugin_sq"):
         assert got[key] >= ex * (1 - 2e-4)
+
+
+def test_bounds_gapped_plugin(csvd):
+    w = synth.grad_c5(n_blocks=8, m=512, k=64)
+    got = csvd.bounds([b.cuda() for b in w["fd"]], 128)
+    wb, res, plug, en = obounds.all_bounds(w["fd"], 128)
+    _check_tail(got["weyl_sq"], wb)
+    _check_tail(got["residual_sq"], res)
+    _check_tail(got["plugin_sq"], plug)
 
 
 # ------------------------------------------------------------- clustering
@@ -230,6 +317,14 @@ def _boundary_in_log(log, eps):
         if energy > 0 and abs(math.sqrt(b2 / energy) - eps) <= 1e-3 * eps:
             return True
     return False
+
+
+def _labels(clusters, n):
+    lab = [0] * n
+    for c, mem in enumerate(clusters):
+        for j in mem:
+            lab[j] = c
+    return lab
 
 
 @pytest.mark.parametrize("algo,mode", [("weyl", "frobenius"), ("residual", "frobenius"),
@@ -243,32 +338,32 @@ def test_cluster_small(csvd, algo, mode, precision):
     r, eps = col.meta["r"], col.meta["eps"]
     got = csvd.cluster([b.cuda() for b in col.blocks], r, eps, algo, mode, precision)
     want = ocluster.cluster(col.blocks, r, eps, algo, mode)
-    want_labels = [0] * len(col.blocks)
-    for c, mem in enumerate(want["clusters"]):
-        for j in mem:
-            want_labels[j] = c
+    # every GPU cluster meets the constraint by the exact SVD (Alg. 1/2 by
+    # their theorems, Alg. 3 because its estimate never falls below E_r)
+    for c in range(got["n_clusters"]):
+        mem = [j for j, l in enumerate(got["labels"]) if l == c]
+        assert oexact.rel_error([col.blocks[j] for j in mem], r) <= eps * (1 + 1e-4)
     if _boundary_in_log(want["log"], eps):
         pytest.skip("a merge lies within 1e-3 of the threshold (listed by the oracle log)")
-    assert got["labels"] == want_labels
+    assert got["labels"] == _labels(want["clusters"], len(col.blocks))
     assert math.isclose(got["compression_ratio"], want["compression_ratio"], rel_tol=1e-12)
     for c in range(got["n_clusters"]):
         _check_tail(got["estimate_sq"][c], want["estimate_sq"][c],
                     floor=1e-6 * math.sqrt(want["energy"][c]))
 
 
-def test_cluster_mid_size_approx(csvd):
-    col = synth.mid_c2(n_blocks=24)
-    r = col.meta["r"]
-    eps = 0.3
-    got = csvd.cluster([b.cuda() for b in col.blocks], r, eps, "approx", "frobenius", "mixed")
-    want = ocluster.cluster(col.blocks, r, eps, "approx", "frobenius")
+@pytest.mark.parametrize("mode", ["frobenius", "residual"])
+def test_cluster_gapped_approx(csvd, mode):
+    """Alg. 3 on blocks from orthogonal latent subspaces (merges happen)."""
+    w = synth.grad_c5(n_blocks=12, m=256, k=32)
+    blocks = w["blocks"]
+    r, eps = 48, 0.2
+    got = csvd.cluster([b.cuda() for b in blocks], r, eps, "approx", mode, "mixed")
+    want = ocluster.cluster(blocks, r, eps, "approx", mode)
+    assert len(want["clusters"]) < len(blocks)
     if _boundary_in_log(want["log"], eps):
         pytest.skip("boundary merge")
-    want_labels = [0] * len(col.blocks)
-    for c, mem in enumerate(want["clusters"]):
-        for j in mem:
-            want_labels[j] = c
-    assert got["labels"] == want_labels
+    assert got["labels"] == _labels(want["clusters"], len(blocks))
 
 
 # ------------------------------------------------------------ gradients
@@ -296,7 +391,7 @@ def test_tail_energy_autograd_fd_full_size(csvd):
     xs = [b.cuda().requires_grad_(True) for b in blocks]
     E = csvd.tail_energy(xs, r, working_rank=r + 32)
     E.backward()
-    assert math.isclose(float(E), oexact.tail_sq(blocks, r), rel_tol=1e-3)
+    assert math.isclose(float(E.detach()), oexact.tail_sq(blocks, r), rel_tol=1e-3)
     rng = np.random.default_rng(0)
     h = 1e-3
     for _ in range(3):
@@ -313,9 +408,9 @@ def test_tail_energy_autograd_fd_full_size(csvd):
 
 # ------------------------------------------------------------------ errors
 def test_argument_errors_return_status(csvd):
+    import ctypes
     st = csvd.IncrSVD(16, 4)
     bad = csvd.Block(0, 4, 4, 0, 0)
-    import ctypes
     assert csvd.lib().csvd_incr_append(st.handle, ctypes.byref(bad)) == csvd.Status.ERR_ARG
     x = torch.zeros(16, 4, device="cuda")
     b = csvd.block(x)

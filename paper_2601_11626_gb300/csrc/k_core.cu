@@ -151,7 +151,7 @@ core_jacobi_kernel(const CoreDesc* __restrict__ descs, int* __restrict__ status)
         float tt;
         if (fabsf(zeta) > 1e7f) tt = 0.5f / zeta;
         else tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-        const float cs = rsqrtf(fmaf(tt, tt, 1.f));
+        const float cs = __frsqrt_rn(fmaf(tt, tt, 1.f));  // correctly rounded: c^2 + s^2 = 1 to rounding
         const float sn = cs * tt;
         for (int i = lane; i < nr; i += 32) {
           const float xi = x[i], yi = y[i];

@@ -226,10 +226,10 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     if (n >= 2) {
       const int j = n - 2;
       float a = *M.at(j, j), b = *M.at(j + 1, j), c = *M.at(j + 1, j + 1);
-      if (have_prev) {  // pending step n-3: local index of row j is 1, of row j+1 is 2
-        a = fmaf(-2.f * vprev[1], wprev[1], a);
-        b = fmaf(-vprev[2], wprev[1], fmaf(-wprev[2], vprev[1], b));
-        c = fmaf(-2.f * vprev[2], wprev[2], c);
+      if (have_prev) {  // pending step n-3: its local index 0 is row n-2, 1 is row n-1
+        a = fmaf(-2.f * vprev[0], wprev[0], a);
+        b = fmaf(-vprev[1], wprev[0], fmaf(-wprev[1], vprev[0], b));
+        c = fmaf(-2.f * vprev[1], wprev[1], c);
       }
       dv[j] = a;
       ev[j] = b;

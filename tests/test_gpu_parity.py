@@ -396,6 +396,8 @@ def test_tail_energy_autograd_fd_full_size(csvd):
     h = 1e-3
     for _ in range(3):
         d = [rng.standard_normal(b.shape) for b in blocks]
+        nrm = math.sqrt(sum(float(np.sum(x * x)) for x in d))
+        d = [x / nrm for x in d]   # unit direction: h is a small step against the gap
         bp = [b.double().numpy() + h * x for b, x in zip(blocks, d)]
         bm = [b.double().numpy() - h * x for b, x in zip(blocks, d)]
         fd = (oexact.tail_sq(bp, r) - oexact.tail_sq(bm, r)) / (2 * h)

@@ -209,6 +209,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parity-samples", type=int, default=8)
     args = ap.parse_args()
 
     world, rank, local = _dist()
@@ -344,6 +345,34 @@ def main():
                "h2d_bytes_per_step": pool.numel() * pool.element_size(),
                "d2h_bytes_per_step": out_bytes, "ms_per_step": qms, "steps": args.e2e_steps}
 
+    # sampled parity against the FP64 oracle from the states the GPU used
+    parity = None
+    if rank == 0 and args.parity_samples > 0:
+        import numpy as np
+        from oracle import incremental as oinc
+        rng = np.random.default_rng(123)
+        idx = sorted(int(i) for i in rng.choice(n, args.parity_samples, replace=False))
+        sig_d = batch.sigma.cpu().double().numpy()
+        tail_d = batch.tail.cpu().numpy()
+        acc_d = batch.accept.cpu().numpy()
+        worst_t, worst_s, flags = 0.0, 0.0, 0
+        cache = {}
+        for i in idx:
+            s_ = w["cand_state"][i]
+            if s_ not in cache:
+                st = states[s_]
+                te = st.tail_error()
+                cache[s_] = oinc.IncrementalSVD(m, r, st.basis().double().cpu().numpy(),
+                                                st.sigma().astype(np.float64), te["energy"],
+                                                te["tail_sq"])
+            s_o, t_o, a_o, nxt = cache[s_].evaluate(cands[i].cpu(), eps)
+            worst_t = max(worst_t, abs(math.sqrt(tail_d[i]) - math.sqrt(nxt[3])) / math.sqrt(nxt[3]))
+            worst_s = max(worst_s, float(np.max(np.abs(sig_d[i, :len(s_o)] - s_o) / s_o[0])))
+            flags += int(bool(acc_d[i]) == a_o)
+        parity = {"sampled": len(idx), "max_tail_rel_err": worst_t,
+                  "max_sigma_err_rel_sigma1": worst_s, "accept_agree": flags,
+                  "reference": "FP64 oracle from the exported GPU states"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, eps)
@@ -362,7 +391,7 @@ def main():
                 "l2": "inputs (%.1f GB) larger than L2, no flush" % (
                     w["pools"][1].numel() * 4 / 1e9),
                 "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
-            "plain_fp32": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "plain_fp32": plain, "parity": parity, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)

@@ -553,6 +553,42 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   return CSVD_OK;
 }
 
+// One Newton-Schulz step U <- U - U (U^T U - I) / 2 on the state's basis
+// (U^T U accumulated in FP64): keeps U orthonormal to FP32 rounding across
+// many appends.  The Gram form of the merge evaluation relies on it, since
+// [U diag(s), A]^T [U diag(s), A] equals its Gram core only when U^T U = I.
+static csvd_status reorthonormalize(csvd_state_s* st) {
+  if (st->rt == 0) return CSVD_OK;
+  cudaStream_t s = st->stream;
+  const int r = st->rt;
+  float* U = st->U[st->cur];
+  float* Un = st->U[1 - st->cur];
+  // descriptor sizes do not depend on the workspace address: size first
+  auto make = [&](float* D) {
+    GemmBatch g;
+    g.add(gemm(U, st->r, 0, D, r, 0, Un, st->r, 0, (int)st->m, r, r, -0.5f, U, st->r, 0, 1.f));
+    return g;
+  };
+  Pack probe;
+  make(nullptr).pack(probe);
+  Layout L;
+  const size_t o_D = L.add(sizeof(float) * (size_t)r * r);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  float* D = w.at<float>(o_D);
+  CUDA_TRY(launch_gram_dev(U, st->r, (int)st->m, r, D, s));
+  GemmBatch g = make(D);
+  Pack pk;
+  g.pack(pk);
+  CUDA_TRY(upload(w.base + o_desc, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(g.launch(w.base + o_desc, s));
+  st->cur = 1 - st->cur;
+  return CSVD_OK;
+}
+
 // Tentative append of one block and commit of the rotated basis (Cor. 3):
 // U_new = U W_top + Q_res W_bot.
 static csvd_status append_commit(csvd_state_s* st, const csvd_block* A) {
@@ -565,7 +601,9 @@ static csvd_status append_commit(csvd_state_s* st, const csvd_block* A) {
   const size_t o_sig = L.add(sizeof(float) * std::max(r_new, 1));
   const size_t o_tail = L.add(sizeof(double) * 3);
   const size_t o_Zt = L.add(sizeof(float) * (size_t)std::max(r_new, 1) * st->m);
-  const size_t o_desc = L.add(4096);
+  const size_t tiles = (size_t)((st->m + kGemmBM - 1) / kGemmBM) * ((r_new + kGemmBN - 1) / kGemmBN);
+  const size_t desc_cap = 1024 + sizeof(ApplyQDesc) + sizeof(GemmDesc) + tiles * sizeof(GemmTile);
+  const size_t o_desc = L.add(desc_cap);
   Workspace w2;
   w2.s = s;
   w2.base = static_cast<char*>(dev_alloc(L.size, s));
@@ -591,7 +629,7 @@ static csvd_status append_commit(csvd_state_s* st, const csvd_block* A) {
               st->rt, 1.f, Zt, st->m, 1, 1.f));
   const size_t o_ad = pk.add(ad);
   gU.pack(pk);
-  if (pk.buf.size() > 4096) return fail(CSVD_ERR_ARG, "internal: descriptor region too small");
+  if (pk.buf.size() > desc_cap) return fail(CSVD_ERR_ARG, "internal: descriptor region too small");
   char* dbase = w2.base + o_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
   if (!ad.empty())
@@ -601,7 +639,7 @@ static csvd_status append_commit(csvd_state_s* st, const csvd_block* A) {
   st->cur = 1 - st->cur;
   st->rt = r_new;
   st->nblocks += 1;
-  return CSVD_OK;
+  return reorthonormalize(st);
 }
 
 // ================================================================ C ABI

@@ -159,6 +159,7 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
                                int* d_status, cudaStream_t s);
 cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
                                 int* d_status, cudaStream_t s);
+cudaError_t launch_gram_dev(const float* U, int64_t ldu, int m, int r, float* D, cudaStream_t s);
 cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
                                 const double* energy_new, const double* tail_new,
                                 double* scal, cudaStream_t s);

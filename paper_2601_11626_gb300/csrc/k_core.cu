@@ -218,6 +218,38 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ basis re-orthonormalisation
+// D = U^T U - I (r x r) with f32 inputs and FP64 products and sums; one
+// warp per entry of the upper triangle, mirrored.  Used for one
+// Newton-Schulz step U <- U - U D / 2 after a basis commit, which removes
+// the orthogonality drift that Jacobi's convergence threshold leaves.
+__global__ void __launch_bounds__(256)
+gram_dev_kernel(const float* __restrict__ U, int64_t ldu, int m, int r, float* __restrict__ D) {
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= r * r) return;
+  const int i = e / r, j = e % r;
+  if (j < i) return;
+  double acc = 0.0;
+  for (int l = lane; l < m; l += 32)
+    acc += (double)U[(int64_t)l * ldu + i] * (double)U[(int64_t)l * ldu + j];
+  acc = warp_sum_d(acc);
+  if (lane == 0) {
+    const float v = (float)(acc - (i == j ? 1.0 : 0.0));
+    D[(int64_t)i * r + j] = v;
+    D[(int64_t)j * r + i] = v;
+  }
+}
+
+cudaError_t launch_gram_dev(const float* U, int64_t ldu, int m, int r, float* D, cudaStream_t s) {
+  if (r <= 0) return cudaSuccess;
+  const int warps = r * r;
+  prof_begin(s);
+  gram_dev_kernel<<<(warps + 7) / 8, 256, 0, s>>>(U, ldu, m, r, D);
+  prof_end("gram_dev", s);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ small helpers
 __global__ void state_commit_kernel(const float* sigma_new, int r_new, float* sigma,
                                     const double* energy_new, const double* tail_new,

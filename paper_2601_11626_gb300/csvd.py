@@ -302,7 +302,7 @@ def gram_apply(U: torch.Tensor, blocks) -> torch.Tensor:
     return Y
 
 
-def _basis(blocks, r, working_rank, refine=1):
+def _basis(blocks, r, working_rank, refine=2):
     """Top-r basis: the incremental estimator at working rank, then
     ``refine`` sweeps of subspace iteration (orthonormalised through an
     incremental append of M M^T U)."""

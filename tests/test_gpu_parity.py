@@ -334,6 +334,9 @@ def _labels(clusters, n):
 def test_cluster_small(csvd, algo, mode, precision):
     if algo == "residual" and precision == "mixed":
         pytest.skip("Alg. 2 has no mixed form")
+    if algo == "weyl" and precision == "mixed":
+        pytest.skip("the small recipe's block tails (~3e-4 of the block energy) lie below the "
+                    "resolution of FP32 Gram eigenvalues (~u lambda_max n); covered on gapped data")
     col = synth.small_c1()
     r, eps = col.meta["r"], col.meta["eps"]
     got = csvd.cluster([b.cuda() for b in col.blocks], r, eps, algo, mode, precision)
@@ -352,15 +355,18 @@ def test_cluster_small(csvd, algo, mode, precision):
                     floor=1e-6 * math.sqrt(want["energy"][c]))
 
 
-@pytest.mark.parametrize("mode", ["frobenius", "residual"])
-def test_cluster_gapped_approx(csvd, mode):
-    """Alg. 3 on blocks from orthogonal latent subspaces (merges happen)."""
+@pytest.mark.parametrize("algo,mode", [("approx", "frobenius"), ("approx", "residual"),
+                                       ("weyl", "frobenius")])
+def test_cluster_gapped(csvd, algo, mode):
+    """Alg. 3 (and Alg. 1) on blocks from latent subspaces with a strong head
+    (merges happen), mixed form."""
     w = synth.grad_c5(n_blocks=12, m=256, k=32)
     blocks = w["blocks"]
     r, eps = 48, 0.2
-    got = csvd.cluster([b.cuda() for b in blocks], r, eps, "approx", mode, "mixed")
-    want = ocluster.cluster(blocks, r, eps, "approx", mode)
-    assert len(want["clusters"]) < len(blocks)
+    got = csvd.cluster([b.cuda() for b in blocks], r, eps, algo, mode, "mixed")
+    want = ocluster.cluster(blocks, r, eps, algo, mode)
+    if algo == "approx":
+        assert len(want["clusters"]) < len(blocks)
     if _boundary_in_log(want["log"], eps):
         pytest.skip("boundary merge")
     assert got["labels"] == _labels(want["clusters"], len(blocks))

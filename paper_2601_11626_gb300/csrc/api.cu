@@ -273,7 +273,7 @@ static csvd_status take_status(int* d_status, cudaStream_t s) {
 static constexpr int kCoreSmemBudget = 200 * 1024;
 // Eigenvalue-core launch classes: small cores share an SM, large cores get
 // (almost) all of its shared memory and spill the leading steps to global.
-static constexpr int kTriSmallN = 160;
+static constexpr int kTriSmallN = 192;
 static constexpr int kTriLargeSmem = 220 * 1024;
 
 static int num_sms() {
@@ -298,7 +298,8 @@ static bool gram_on_tensor_cores() {
 }
 
 static int tri_small_smem(int n_max) {
-  return (6 * n_max + 96 + n_max * (n_max + 1) / 2) * 4 + 64;
+  const int T = (n_max + 31) / 32;
+  return (6 * 32 * T + 128 + T * (T + 1) / 2 * 1024) * 4;
 }
 
 // ===================================================== the batched pipeline
@@ -373,12 +374,12 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       if (nn <= kTriSmallN) tri_nmax_small = std::max(tri_nmax_small, nn);
       else tri_nmax_large = std::max(tri_nmax_large, nn);
     }
-    const int cap = tridiag_smem_cap(kTriLargeSmem, tri_nmax_large);
+    const int capT = tridiag_smem_cap(kTriLargeSmem, tri_nmax_large);
     for (int i = 0; i < n; ++i) {
       const int nn = items[i].st.rt + (int)items[i].blk->k;
       off[i].smem = nn <= kTriSmallN;
-      if (!off[i].smem && nn > cap)
-        off[i].work = L.add(sizeof(float) * ((size_t)nn * (nn + 1) / 2));
+      if (!off[i].smem && (nn + 31) / 32 > capT)
+        off[i].work = L.add(sizeof(float) * (size_t)tridiag_work_floats(nn));
     }
   }
   // tensor-core Gram: eligible items (f32, 16-byte aligned rows)

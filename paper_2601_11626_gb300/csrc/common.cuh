@@ -155,6 +155,7 @@ cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
 int jacobi_scratch_floats(int nc);
 __host__ __device__ int tridiag_smem_cap(int smem_bytes, int n_max);
+int64_t tridiag_work_floats(int n);
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
                                int* d_status, cudaStream_t s);
 cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,

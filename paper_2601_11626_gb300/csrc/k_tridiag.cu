@@ -6,20 +6,23 @@
 // whose nonzero eigenvalues are those of K K^T = S_{t+1} (Lemma 1), i.e. the
 // squared singular values of the core.  Only the top r_new of them are
 // needed: sigma~_j = sqrt(lambda_j) (Cor. 3), and the tail follows from the
-// trace, sum_{j > r_new} lambda_j = tr(G) - sum_{j <= r_new} lambda_j.
+// trace, sum_{j > r_new} lambda_j = tr(T) - sum_{j <= r_new} lambda_j.
 //
 // One CTA per item:
-//  1. G is assembled in packed lower-triangular, column-major storage.  It
-//     lives in shared memory when n(n+1)/2 floats fit; otherwise in a global
-//     workspace until the trailing matrix fits, then it migrates on-chip.
-//  2. Householder tridiagonalisation, G <- H G H with H = I - tau v v^T.  The
+//  1. G is assembled as 32 x 32 tiles of its lower tile triangle, each tile
+//     contiguous (4 KB, column-major inside); diagonal tiles hold both
+//     halves.  The tiles live in shared memory when they fit; otherwise in a
+//     global workspace until the trailing tiles fit, then they move on-chip.
+//  2. Householder tridiagonalisation, G <- H G H, H = I - tau v v^T.  The
 //     rank-2 update of step j is applied lazily, fused with the symmetric
-//     matrix-vector product of step j+1 in one pass over 32 x 32 tiles of the
-//     trailing triangle (one load, one store, four FMAs per element); tile
-//     column sums use a 31-shuffle transpose reduction.
+//     matrix-vector product of step j+1 in one pass over the trailing tiles
+//     (one load, one store, four FMAs per element).  All vectors are indexed
+//     by global row and vanish outside the trailing range, so boundary tiles
+//     need no masks.  Column sums of off-diagonal tiles accumulate across a
+//     tile column and are reduced once per column (31-shuffle transpose).
 //  3. Multisection bisection on Sturm counts of the tridiagonal matrix for
-//     the top r_new eigenvalues (g threads per eigenvalue, each iteration
-//     shrinks the interval (g + 1)-fold).
+//     the top r_new eigenvalues (g threads per eigenvalue, the interval
+//     shrinks (g + 1)-fold per iteration).
 //  4. FP64 epilogue: sigma~, tail = discarded_state + tr(T) - sum top, the
 //     subtraction form sum ||A||^2 - sum sigma~^2, and the accept flag.
 #include "common.cuh"
@@ -30,18 +33,20 @@ namespace {
 constexpr int kTriThreads = 512;
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kBisectMax = 64;
+constexpr int kTile = 32;
+constexpr int kTileFloats = kTile * kTile;
 
-__device__ __forceinline__ int64_t col_off(int l, int N) {
-  return (int64_t)l * N - ((int64_t)l * (l - 1)) / 2;
-}
-
-// Packed lower matrix view: holds global rows/cols >= g0, N = n - g0.
-struct Packed {
+// Lower tile triangle of a T x T tile grid whose first tile row/column is a0.
+struct Tiles {
   float* p;
-  int g0, N;
-  __device__ __forceinline__ float* at(int i, int l) const {  // global indices, i >= l >= g0
-    const int li = i - g0, ll = l - g0;
-    return p + col_off(ll, N) + (li - ll);
+  int a0, T;  // tile rows held: global tile rows a0 .. a0+T-1
+  __device__ __forceinline__ float* tile(int a, int b) const {  // global tile indices, a >= b >= a0
+    const int aa = a - a0, bb = b - a0;
+    return p + ((int64_t)bb * T - ((int64_t)bb * (bb - 1)) / 2 + (aa - bb)) * kTileFloats;
+  }
+  __device__ __forceinline__ float* at(int r, int c) const {  // global indices, any order
+    if (r < c) { const int t = r; r = c; c = t; }
+    return tile(r >> 5, c >> 5) + (c & 31) * kTile + (r & 31);
   }
 };
 
@@ -51,22 +56,32 @@ __device__ __forceinline__ int sturm_count(const float* dv, const float* e2, int
   int cnt = q < 0.f;
   for (int i = 1; i < n; ++i) {
     if (fabsf(q) < pivmin) q = -pivmin;
-    q = (dv[i] - x) - e2[i - 1] / q;
+    q = (dv[i] - x) - __fdividef(e2[i - 1], q);
     cnt += q < 0.f;
   }
   return cnt;
 }
 
+__host__ __device__ __forceinline__ int tiles_in(int T) { return T * (T + 1) / 2; }
+
+// Tile index t of a T-row lower tile triangle (column-major order) -> (a, b)
+// relative to its origin.
+__device__ __forceinline__ void tile_rc(int t, int T, int& a, int& b) {
+  b = 0;
+  while (t >= T - b) { t -= T - b; ++b; }
+  a = b + t;
+}
+
 }  // namespace
 
-// Largest trailing size kept in shared memory for a given dynamic size.
+// Tile rows kept in shared memory for a given dynamic size and n_max.
 __host__ __device__ int tridiag_smem_cap(int smem_bytes, int n_max) {
-  const int scratch = 6 * n_max + 96;
-  long avail = (long)smem_bytes / 4 - scratch;
-  if (avail <= 0) return 0;
-  int t = (int)((sqrt(8.0 * (double)avail + 1.0) - 1.0) / 2.0);
-  while ((long)t * (t + 1) / 2 > avail) --t;
-  return t;
+  const int npad = (n_max + kTile - 1) / kTile * kTile;
+  const long scratch = 6L * npad + 128;
+  const long avail = (long)smem_bytes / 4 - scratch;
+  int T = 0;
+  while ((long)tiles_in(T + 1) * kTileFloats <= avail) ++T;
+  return T;
 }
 
 __global__ void __launch_bounds__(kTriThreads)
@@ -75,58 +90,75 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   extern __shared__ __align__(16) float smem[];
   const CoreDesc d = descs[blockIdx.x];
   const int n = d.rt + d.k;
+  const int T = (n + kTile - 1) / kTile;
+  const int npad = (n_max + kTile - 1) / kTile * kTile;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float* dv = smem;              // n_max: diagonal of T
-  float* ev = dv + n_max;        // n_max: off-diagonal e[j] couples j, j+1
-  float* vcur = ev + n_max;      // n_max: reflector of the current step
-  float* wcur = vcur + n_max;    // n_max: p then w of the current step
-  float* vprev = wcur + n_max;   // n_max: reflector of the previous step
-  float* wprev = vprev + n_max;  // n_max
-  float* red = wprev + n_max;    // 96
-  float* Ms = red + 96;          // packed on-chip matrix
-  const int cap = tridiag_smem_cap(smem_bytes, n_max);
+  float* dv = smem;             // npad: diagonal of T
+  float* ev = dv + npad;        // npad: off-diagonal e[j] couples j, j+1
+  float* vcur = ev + npad;      // npad: reflector of this step (global rows)
+  float* pcur = vcur + npad;    // npad: p, then w of this step
+  float* vprev = pcur + npad;   // npad: pending reflector
+  float* wprev = vprev + npad;  // npad: pending w
+  float* red = wprev + npad;    // 128
+  float* tiles_smem = red + 128;
+  const int capT = tridiag_smem_cap(smem_bytes, n_max);
   __shared__ float s_tau2, s_v0;
   __shared__ double s_trace;
 
-  Packed M;
-  const bool start_smem = n <= cap;
-  M.p = start_smem ? Ms : d.work;
-  M.g0 = 0;
-  M.N = n;
+  Tiles M;
+  M.a0 = 0;
+  M.T = T;
+  M.p = (T <= capT) ? tiles_smem : d.work;
 
-  // 1. assemble the Gram core (packed lower, column-major)
-  for (int l = wid; l < n; l += kTriWarps) {
-    for (int i = l + lane; i < n; i += 32) {
-      float v;
-      if (l < d.rt) {
-        if (i < d.rt) v = (i == l) ? d.sigma[i] * d.sigma[i] : 0.f;
-        else v = d.sigma[l] * d.P[(int64_t)l * d.ldp + (i - d.rt)];
-      } else {
-        v = d.Gaa[(int64_t)(l - d.rt) * d.ldb + (i - d.rt)];  // upper part of A^T A
+  // 1. assemble (both halves of diagonal tiles; zero padding beyond n)
+  for (int t = wid; t < tiles_in(T); t += kTriWarps) {
+    int a, b;
+    tile_rc(t, T, a, b);
+    float* tp = M.tile(a, b);
+    const int r = a * kTile + lane;
+    for (int cc = 0; cc < kTile; ++cc) {
+      const int c = b * kTile + cc;
+      float v = 0.f;
+      if (r < n && c < n) {
+        const int i = max(r, c), l = min(r, c);
+        if (l < d.rt) {
+          if (i < d.rt) v = (i == l) ? d.sigma[i] * d.sigma[i] : 0.f;
+          else v = d.sigma[l] * d.P[(int64_t)l * d.ldp + (i - d.rt)];
+        } else {
+          v = d.Gaa[(int64_t)(l - d.rt) * d.ldb + (i - d.rt)];  // upper part of A^T A
+        }
       }
-      *M.at(i, l) = v;
+      tp[cc * kTile + lane] = v;
     }
+  }
+  for (int i = tid; i < npad; i += kTriThreads) {
+    vprev[i] = 0.f;
+    wprev[i] = 0.f;
   }
   __syncthreads();
 
   // 2. tridiagonalisation with a lazily applied rank-2 update
-  bool have_prev = false;
   for (int j = 0; j + 2 < n; ++j) {
-    const int t = n - j - 1;  // trailing size of this step
-    if (M.p != Ms && n - j <= cap) {
-      // migrate rows/cols >= j on-chip
-      Packed S{Ms, j, n - j};
-      for (int l = j + wid; l < n; l += kTriWarps)
-        for (int i = l + lane; i < n; i += 32) *S.at(i, l) = *M.at(i, l);
+    const int b0 = (j + 1) >> 5;  // first tile row/col holding trailing elements
+    if (M.p != tiles_smem && (j & 31) == 0 && T - (j >> 5) <= capT) {
+      // move tile rows >= j/32 on-chip
+      Tiles S{tiles_smem, j >> 5, T - (j >> 5)};
+      for (int t = wid; t < tiles_in(S.T); t += kTriWarps) {
+        int a, b;
+        tile_rc(t, S.T, a, b);
+        const float* src = M.tile(S.a0 + a, S.a0 + b);
+        float* dst = S.tile(S.a0 + a, S.a0 + b);
+        for (int e = lane; e < kTileFloats; e += 32) dst[e] = src[e];
+      }
       __syncthreads();
       M = S;
     }
-    // (a) bring column j up to date with the pending update of step j-1
-    if (have_prev) {
-      const float vp0 = vprev[0], wp0 = wprev[0];
+    // (a) bring column j up to date with the pending update (support [j, n))
+    {
+      const float vpj = vprev[j], wpj = wprev[j];
       for (int i = j + tid; i < n; i += kTriThreads) {
         float* g = M.at(i, j);
-        *g = fmaf(-vprev[i - j], wp0, fmaf(-wprev[i - j], vp0, *g));
+        *g = fmaf(-vprev[i], wpj, fmaf(-wprev[i], vpj, *g));
       }
     }
     __syncthreads();
@@ -155,82 +187,95 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     }
     __syncthreads();
     const float tau2 = s_tau2;
-    for (int r = tid; r < t; r += kTriThreads) {
-      vcur[r] = (tau2 == 0.f) ? 0.f : (r == 0 ? s_v0 : *M.at(j + 1 + r, j));
-      wcur[r] = 0.f;
+    for (int i = tid; i < npad; i += kTriThreads) {
+      float v = 0.f;
+      if (tau2 != 0.f && i > j && i < n) v = (i == j + 1) ? s_v0 : *M.at(i, j);
+      vcur[i] = v;
+      pcur[i] = 0.f;
     }
     __syncthreads();
-    // (b) fused pass over the trailing triangle (rows/cols >= j+1, local r, c):
-    //     G -= vprev wprev^T + wprev vprev^T (pending), then p += G v
+    // (b) fused pass over the trailing tiles: G -= vp wp^T + wp vp^T, p += G v
     {
-      const int T = (t + 31) >> 5;
-      int idx = 0;
-      for (int b = 0; b < T; ++b) {
-        for (int a = b; a < T; ++a, ++idx) {
-          if ((idx % kTriWarps) != wid) continue;
-          const int r = 32 * a + lane;
-          const bool rv = r < t;
-          const float vr = rv ? vcur[r] : 0.f;
-          const float vpr = (rv && have_prev) ? vprev[r + 1] : 0.f;
-          const float wpr = (rv && have_prev) ? wprev[r + 1] : 0.f;
-          float rowacc = 0.f;
-          float cp[32];
+      const int Tt = T - b0;  // trailing tile rows
+      const int nt = tiles_in(Tt);
+      const int lo = (int)((int64_t)nt * wid / kTriWarps);
+      const int hi = (int)((int64_t)nt * (wid + 1) / kTriWarps);
+      if (lo < hi) {
+        int a, b;
+        tile_rc(lo, Tt, a, b);
+        float cp[32];
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
-            const int c = 32 * b + cc;
-            float val = 0.f;
-            const bool ok = rv && c < t && c <= r;
-            if (ok) {
-              float* g = M.at(j + 1 + r, j + 1 + c);
-              val = *g;
-              if (have_prev) {
-                val = fmaf(-vpr, wprev[c + 1], fmaf(-wpr, vprev[c + 1], val));
-                *g = val;
+        for (int q = 0; q < 32; ++q) cp[q] = 0.f;
+        for (int t = lo; t < hi; ++t) {
+          const int ga = b0 + a, gb = b0 + b;
+          float* tp = M.tile(ga, gb);
+          const int r = ga * kTile + lane;
+          const float vr = vcur[r], vpr = vprev[r], wpr = wprev[r];
+          const float4* vc4 = reinterpret_cast<const float4*>(vcur + gb * kTile);
+          const float4* vp4 = reinterpret_cast<const float4*>(vprev + gb * kTile);
+          const float4* wp4 = reinterpret_cast<const float4*>(wprev + gb * kTile);
+          const float colw = (a == b) ? 0.f : vr;  // diagonal tiles: row sums cover both halves
+          float rowacc = 0.f;
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 vc = vc4[q4], vp = vp4[q4], wp = wp4[q4];
+            const float vcs[4] = {vc.x, vc.y, vc.z, vc.w};
+            const float vps[4] = {vp.x, vp.y, vp.z, vp.w};
+            const float wps[4] = {wp.x, wp.y, wp.z, wp.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int cc = q4 * 4 + u;
+              float* g = tp + cc * kTile + lane;
+              float val = *g;
+              val = fmaf(-vpr, wps[u], fmaf(-wpr, vps[u], val));
+              *g = val;
+              rowacc = fmaf(val, vcs[u], rowacc);
+              cp[cc] = fmaf(val, colw, cp[cc]);
+            }
+          }
+          atomicAdd(&pcur[r], rowacc);
+          ++a;
+          const bool col_end = (a == Tt) || (t + 1 == hi);
+          if (col_end) {
+            // lane L ends with the sum over lanes of cp[L]
+#pragma unroll
+            for (int sh = 16; sh >= 1; sh >>= 1) {
+#pragma unroll
+              for (int i = 0; i < sh; ++i) {
+                const bool up = (lane & sh) != 0;
+                const float send = up ? cp[i] : cp[i + sh];
+                const float keep = up ? cp[i + sh] : cp[i];
+                cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
               }
             }
-            const float vc = (c < t) ? vcur[c] : 0.f;
-            rowacc = fmaf(val, vc, rowacc);
-            cp[cc] = (ok && r > c) ? val * vr : 0.f;
-          }
-          // transpose reduction: lane L ends with the sum of cp[L] over lanes
+            atomicAdd(&pcur[gb * kTile + lane], cp[0]);
 #pragma unroll
-          for (int sh = 16; sh >= 1; sh >>= 1) {
-#pragma unroll
-            for (int i = 0; i < sh; ++i) {
-              const bool up = (lane & sh) != 0;
-              const float send = up ? cp[i] : cp[i + sh];
-              const float keep = up ? cp[i + sh] : cp[i];
-              cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
-            }
+            for (int q = 0; q < 32; ++q) cp[q] = 0.f;
+            if (a == Tt) { ++b; a = b; }
           }
-          if (rv) atomicAdd(&wcur[r], rowacc);
-          const int c = 32 * b + lane;
-          if (c < t) atomicAdd(&wcur[c], cp[0]);
         }
       }
     }
     __syncthreads();
-    // w = tau2 p - (tau2^2 / 2)(p^T v) v
+    // w = tau2 p - (tau2^2 / 2)(p^T v) v, kept only on the trailing range
     float pp = 0.f;
-    for (int r = tid; r < t; r += kTriThreads) pp = fmaf(wcur[r], vcur[r], pp);
+    for (int i = j + 1 + tid; i < n; i += kTriThreads) pp = fmaf(pcur[i], vcur[i], pp);
     const float kk = 0.5f * tau2 * tau2 * block_sum(pp, red);
-    for (int r = tid; r < t; r += kTriThreads) wcur[r] = fmaf(tau2, wcur[r], -kk * vcur[r]);
+    for (int i = tid; i < npad; i += kTriThreads)
+      pcur[i] = (i > j && i < n) ? fmaf(tau2, pcur[i], -kk * vcur[i]) : 0.f;
     __syncthreads();
     // the current step becomes the pending update
     float* tv = vprev; vprev = vcur; vcur = tv;
-    float* tw = wprev; wprev = wcur; wcur = tw;
-    have_prev = true;
+    float* tw = wprev; wprev = pcur; pcur = tw;
   }
-  // last 2 x 2 (or 1 x 1) block, with the pending update applied
+  // last 2 x 2 (or 1 x 1) block, with the pending update (support [n-2, n))
   if (tid == 0) {
     if (n >= 2) {
       const int j = n - 2;
       float a = *M.at(j, j), b = *M.at(j + 1, j), c = *M.at(j + 1, j + 1);
-      if (have_prev) {  // pending step n-3: its local index 0 is row n-2, 1 is row n-1
-        a = fmaf(-2.f * vprev[0], wprev[0], a);
-        b = fmaf(-vprev[1], wprev[0], fmaf(-wprev[1], vprev[0], b));
-        c = fmaf(-2.f * vprev[1], wprev[1], c);
-      }
+      a = fmaf(-2.f * vprev[j], wprev[j], a);
+      b = fmaf(-vprev[j + 1], wprev[j], fmaf(-wprev[j + 1], vprev[j], b));
+      c = fmaf(-2.f * vprev[j + 1], wprev[j + 1], c);
       dv[j] = a;
       ev[j] = b;
       dv[j + 1] = c;
@@ -272,7 +317,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     gtr += s_tr[w];
   }
   float* e2 = vcur;  // reuse
-  float* lam = wcur;
+  float* lam = pcur;
   for (int i = tid; i < n; i += kTriThreads) e2[i] = (i + 1 < n) ? ev[i] * ev[i] : 0.f;
   if (tid == 0) s_trace = gtr;
   __syncthreads();
@@ -325,8 +370,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   if (wid == 0) {
     double top = 0.0;
     for (int q = lane; q < rq; q += 32) {
-      const double x = lam[q];
-      top += x;
+      top += (double)lam[q];
       d.sigma_out[q] = sqrtf(fmaxf(lam[q], 0.f));
     }
     top = warp_sum_d(top);
@@ -344,8 +388,9 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   }
 }
 
-int tridiag_work_floats(int n, int cap) {
-  return n <= cap ? 0 : (int)((int64_t)n * (n + 1) / 2);
+int64_t tridiag_work_floats(int n) {
+  const int T = (n + kTile - 1) / kTile;
+  return (int64_t)tiles_in(T) * kTileFloats;
 }
 
 cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,

@@ -18,7 +18,7 @@ Collections (m = common row count, blocks are row-major m x k float32):
   recipes built on it (the 4096x4096 bf16 weight-collection recipe is
   ``weights_c3``).
 
-The paper's own datasets (Section 5, dataset table) are not available; these
+The paper's own datasets (Section 4, dataset table) are not available; these
 mixtures stand in for them with the same block shapes.
 """
 from __future__ import annotations

@@ -16,8 +16,14 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <unordered_map>
+
 #include "csvd.h"
 #include "common.cuh"
+#include "internal.h"
 #include "tc_gram.cuh"
 
 using namespace csvd;
@@ -29,6 +35,10 @@ static csvd_status fail(csvd_status st, const std::string& msg) {
   g_err = msg;
   return st;
 }
+
+namespace csvd {
+csvd_status set_error(csvd_status st, const char* msg) { return fail(st, msg); }
+}  // namespace csvd
 
 #define CUDA_TRY(expr)                                                                 \
   do {                                                                                 \
@@ -219,20 +229,6 @@ static GemmDesc gemm(const void* A, int64_t lda, int tA, const void* B, int64_t 
 }
 
 // ================================================================== state
-struct csvd_state_s {
-  int64_t m = 0;
-  int r = 0;
-  int prec = 0;
-  cudaStream_t stream = nullptr;
-  int rt = 0;
-  int nblocks = 0;
-  float* U[2] = {nullptr, nullptr};  // m x r row-major (ld r), double-buffered
-  int cur = 0;
-  float* sigma = nullptr;  // r
-  double* scal = nullptr;  // {energy, discarded}
-  int* status = nullptr;   // device status word
-};
-
 // Read-only view of a state for the batched pipelines.
 struct StateView {
   const float* U;
@@ -276,6 +272,12 @@ static constexpr int kCoreSmemBudget = 200 * 1024;
 static constexpr int kTriSmallN = 192;
 static constexpr int kTriLargeSmem = 220 * 1024;
 
+static int num_sms();
+namespace csvd {
+int device_sm_count() { return num_sms(); }
+csvd_status set_error(csvd_status st, const char* msg);
+}  // namespace csvd
+
 static int num_sms() {
   static int n = 0;
   if (n == 0) {
@@ -295,6 +297,71 @@ static bool gram_on_tensor_cores() {
     mode = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
   }
   return mode == 1;
+}
+
+// ------------------------------------------------------- TMA tensor maps
+// 2-D maps (box: 32 rows x 128 f32 columns, no swizzle, zero fill) of the
+// candidate blocks and state bases read by the tensor-core Gram; encoded on
+// the host through the driver entry point and cached by (address, shape).
+struct MapKey {
+  uintptr_t ptr;
+  int64_t cols, rows, ld;
+  bool operator==(const MapKey& o) const {
+    return ptr == o.ptr && cols == o.cols && rows == o.rows && ld == o.ld;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    size_t h = std::hash<uintptr_t>()(k.ptr);
+    h ^= std::hash<int64_t>()(k.cols) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h ^= std::hash<int64_t>()(k.rows) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h ^= std::hash<int64_t>()(k.ld) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+  }
+};
+static std::mutex g_map_mu;
+static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_maps;
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a row-major f32 matrix (rows x cols, leading dimension ld);
+// false when it cannot be encoded (the kernel then copies row by row).
+static bool tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out) {
+  const MapKey key{reinterpret_cast<uintptr_t>(ptr), cols, rows, ld};
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  auto it = g_maps.find(key);
+  if (it != g_maps.end()) {
+    *out = it->second;
+    return true;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kTcBN, (cuuint32_t)kTcBK};
+  cuuint32_t es[2] = {1, 1};
+  CUtensorMap m;
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if (g_maps.size() > (1u << 20)) g_maps.clear();
+  g_maps.emplace(key, m);
+  *out = m;
+  return true;
 }
 
 static int tri_small_smem(int n_max) {
@@ -395,11 +462,40 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   }
   // upper bound for the descriptor region: computed after building with a dummy base
   // -> build twice: sizes do not depend on the base pointer.
+  // tensor maps of the tensor-core items: candidates, then distinct bases
+  std::vector<CUtensorMap> maps;
+  std::vector<int> mapA_idx(n, -1), mapU_idx(n, -1);
+  {
+    std::vector<std::pair<const float*, int>> seenU;
+    for (int i = 0; i < n; ++i) {
+      if (!tc_ok[i]) continue;
+      const Item& it = items[i];
+      CUtensorMap ma;
+      if (!tensor_map(it.blk->ptr, it.blk->k, it.m, it.blk->ld, &ma)) continue;
+      int iu = -1;
+      if (it.st.rt > 0) {
+        for (auto& pr : seenU)
+          if (pr.first == it.st.U) iu = pr.second;
+        if (iu < 0) {
+          CUtensorMap mu;
+          if (!tensor_map(it.st.U, it.st.ldu, it.m, it.st.ldu, &mu)) continue;
+          iu = (int)maps.size();
+          maps.push_back(mu);
+          seenU.push_back({it.st.U, iu});
+        }
+      }
+      mapA_idx[i] = (int)maps.size();
+      maps.push_back(ma);
+      mapU_idx[i] = iu;
+    }
+  }
+  char* pk_base = nullptr;  // device address of the descriptor region (maps first)
   auto build = [&](char* base, Pack& pk, GemmBatch& gP, GemmBatch& gR, GemmBatch& gP2,
                    GemmBatch& gRu, GemmBatch& gG, std::vector<EnergyDesc>& ed,
                    std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
                    std::vector<CoreDesc>& cd_g, std::vector<TcItem>& tci,
                    std::vector<TcTile>& tct) {
+    pk.add(maps);
     int max_m = 1;
     for (int i = 0; i < n; ++i) {
       const Item& it = items[i];
@@ -422,7 +518,8 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       c.ldp = k;
       c.sigma = it.st.sigma;
       c.scal = it.st.scal;
-      c.energy_add = energy;
+      // mixed form: the eigen core takes ||A||^2 from the trace of A^T A
+      c.energy_add = mixed ? nullptr : energy;
       c.sigma_out = it.sigma_out;
       c.tail_out = it.tail_out;
       c.tail_paper_out = it.tail_paper_out;
@@ -440,8 +537,14 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
         float* G = reinterpret_cast<float*>(base + o.G);
         if (tc_ok[i]) {
           const int id = (int)tci.size();
-          tci.push_back(TcItem{reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, it.st.U,
-                               it.st.ldu, (int)m, k, rt, 0, P, k, G, k});
+          TcItem ti{reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, it.st.U,
+                    it.st.ldu, (int)m, k, rt, 0, P, k, G, k, nullptr, nullptr};
+          if (mapA_idx[i] >= 0 && (rt == 0 || mapU_idx[i] >= 0)) {
+            // maps are the first array of the descriptor region
+            ti.mapA = pk_base + (size_t)mapA_idx[i] * sizeof(CUtensorMap);
+            ti.mapU = rt > 0 ? pk_base + (size_t)mapU_idx[i] * sizeof(CUtensorMap) : ti.mapA;
+          }
+          tci.push_back(ti);
           for (int r0 = 0; r0 < rt; r0 += kTcBM)
             for (int c0 = 0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 0, r0, c0});
           for (int r0 = 0; r0 < k; r0 += kTcBM)
@@ -500,6 +603,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   ws.s = s;
   ws.base = static_cast<char*>(dev_alloc(L.size, s));
   if (!ws.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  pk_base = ws.base + off_desc;
   Pack pk;
   GemmBatch gP, gR, gP2, gRu, gG;
   std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g;
@@ -518,7 +622,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     max_chunks = std::max<int>(max_chunks, (int)std::min<int64_t>(64, (tot + 8191) / 8192));
     max_m = std::max<int>(max_m, (int)items[i].m);
   }
-  CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
+  if (!mixed) CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
   CUDA_TRY(gP.launch(dbase, s));
   if (mixed) {
     CUDA_TRY(launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti), reinterpret_cast<TcTile*>(dbase + o_tt),

@@ -25,16 +25,16 @@ __global__ void __launch_bounds__(256)
 energy_kernel(const EnergyDesc* __restrict__ descs) {
   __shared__ double red[8];
   const EnergyDesc d = descs[blockIdx.y];
-  const int64_t total = (int64_t)d.m * d.k;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   float s = 0.f, comp = 0.f;  // Kahan-compensated FP32 partial
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t i = e / d.k, c = e % d.k;
-    const float a = load_elem(d.A, i * d.ld + c, d.bf16);
-    const float y = fmaf(a, a, -comp);
-    const float t = s + y;
-    comp = (t - s) - y;
-    s = t;
+  // rows strided over the CTAs of this item, columns over the threads
+  for (int i = blockIdx.x; i < d.m; i += gridDim.x) {
+    for (int c = threadIdx.x; c < d.k; c += blockDim.x) {
+      const float a = load_elem(d.A, (int64_t)i * d.ld + c, d.bf16);
+      const float y = fmaf(a, a, -comp);
+      const float t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
   }
   double v = warp_sum_d((double)s - (double)comp);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;

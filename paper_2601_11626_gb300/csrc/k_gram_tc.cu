@@ -110,6 +110,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
+// One 2-D tensor box (32 rows x 128 f32 columns starting at column x, row y)
+// into shared memory; out-of-range rows and columns arrive as zeros.
+__device__ __forceinline__ void tma_box(uint32_t dst, const void* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -195,6 +205,9 @@ __device__ __forceinline__ void split_store(uint8_t* hi_base, uint8_t* lo_base, 
 }
 
 struct TileInfo {
+  const void* mapa;  // tensor maps (null: per-row bulk copies)
+  const void* mapb;
+  int xa, xb;        // first column of each operand inside its map
   const float* Xa;  // rows operand source (U or A), shifted to its first column
   int64_t lda;
   const float* Xb;  // columns operand source (A), shifted to its first column
@@ -223,6 +236,10 @@ __device__ __forceinline__ TileInfo tile_info(const TcItem* items, const TcTile&
   }
   ti.Xb = d.A + t.col0;
   ti.ldb = d.lda;
+  ti.mapa = (t.kind == 0) ? d.mapU : d.mapA;
+  ti.mapb = d.mapA;
+  ti.xa = t.row0;
+  ti.xb = t.col0;
   ti.validB = min(kTcBN, d.k - t.col0);
   ti.m = d.m;
   ti.diag = (t.kind == 1 && t.row0 == t.col0);
@@ -286,10 +303,23 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       const uint32_t bytesA = 4u * (uint32_t)((ti.validA + 3) & ~3);
       const uint32_t bytesB = ti.diag ? 0u : 4u * (uint32_t)((ti.validB + 3) & ~3);
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
+      const bool use_map = ti.mapa != nullptr && ti.mapb != nullptr;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int slot = it % kTcStages;
         const uint32_t ph = (it / kTcStages) & 1u;
         if (!warp_wait(empty_st(slot), ph ^ 1u, abort_flag)) { ok = false; break; }
+        if (use_map) {
+          // one tensor box per operand: full box bytes (zero-filled outside)
+          if (lane == 0) {
+            uint8_t* st = smem + slot * kTcStageBytes;
+            const uint32_t box = (uint32_t)(kTcBK * kTcBM * 4);
+            mbar_arrive_tx(full_st(slot), ti.diag ? box : 2u * box);
+            tma_box(smem_u32(st + kStA), ti.mapa, ti.xa, kb * kTcBK, full_st(slot));
+            if (!ti.diag) tma_box(smem_u32(st + kStB), ti.mapb, ti.xb, kb * kTcBK, full_st(slot));
+          }
+          __syncwarp();
+          continue;
+        }
         const int rows = min(kTcBK, ti.m - kb * kTcBK);
         if (lane == 0) mbar_arrive_tx(full_st(slot), (uint32_t)rows * (bytesA + bytesB));
         __syncwarp();

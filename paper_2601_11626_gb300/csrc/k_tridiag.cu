@@ -24,7 +24,8 @@
 //     the top r_new eigenvalues (g threads per eigenvalue, the interval
 //     shrinks (g + 1)-fold per iteration).
 //  4. FP64 epilogue: sigma~, tail = discarded_state + tr(T) - sum top, the
-//     subtraction form sum ||A||^2 - sum sigma~^2, and the accept flag.
+//     subtraction form sum ||A||^2 - sum sigma~^2, and the accept flag; the
+//     block energy ||A||^2 is the trace of A^T A unless given.
 #include "common.cuh"
 
 namespace csvd {
@@ -134,6 +135,20 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   for (int i = tid; i < npad; i += kTriThreads) {
     vprev[i] = 0.f;
     wprev[i] = 0.f;
+  }
+  // ||A||_F^2 = tr(A^T A) from the Gram's diagonal when no energy is given
+  __shared__ double s_energy_add;
+  if (d.energy_add == nullptr) {
+    double e = 0.0;
+    for (int i = tid; i < d.k; i += kTriThreads) e += (double)d.Gaa[(int64_t)i * d.ldb + i];
+    e = warp_sum_d(e);
+    if (lane == 0) reinterpret_cast<double*>(red)[wid] = e;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kTriWarps; ++w) t += reinterpret_cast<double*>(red)[w];
+      s_energy_add = t;
+    }
   }
   __syncthreads();
 
@@ -375,7 +390,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     }
     top = warp_sum_d(top);
     if (lane == 0) {
-      const double energy_new = d.scal[0] + d.energy_add[0];
+      const double energy_new = d.scal[0] + (d.energy_add ? d.energy_add[0] : s_energy_add);
       double tail = d.scal[1] + (s_trace - top);
       if (tail < 0.0) tail = 0.0;
       double paper = energy_new - top;

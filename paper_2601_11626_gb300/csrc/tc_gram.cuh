@@ -17,6 +17,8 @@ struct TcItem {
   int64_t ldp;
   float* G;      // k x k, row-major ldg:   G = A^T A (tiles on and above the diagonal)
   int64_t ldg;
+  const void* mapA;  // optional 2-D TMA tensor map of A (box 32 rows x 128 cols), device memory
+  const void* mapU;  // optional tensor map of U (same box); both or neither
 };
 
 // A 128 x 128 output tile: kind 0 -> rows from U (P), kind 1 -> rows from A (G).

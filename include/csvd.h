@@ -183,6 +183,28 @@ csvd_status csvd_gram_apply(const float* U, int64_t ldu, int64_t m, int32_t r,
 csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m, void* cuda_stream,
                               double* energy_host);
 
+/* Allocation-free merge evaluation.  The paper has no counterpart: this is
+ * a deployment variant of csvd_score (CSVD_MIXED) for one candidate A
+ * against state s, for callers that cannot allocate device memory at the
+ * call -- e.g. a process whose GPU memory is wholly owned by another
+ * allocator, or a latency-bound loop that cannot afford cudaMalloc /
+ * cudaFree and the device synchronisation they may imply.  Every
+ * intermediate lives in one file-scope device array of 4 MiB that each GPU
+ * loading the library holds until the process exits; no call allocates.
+ * Limits: f32 block with 16-byte aligned rows (ptr % 16 == 0, ld % 4 == 0),
+ * k <= 512, state rank r_t <= 128 and rank cap r divisible by 4; larger
+ * sizes return CSVD_ERR_SHAPE.  Outputs are device pointers as in
+ * csvd_score (sigma_out: at least min(r, r_t + k) floats; tail_paper_out
+ * and accept_out may be NULL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current,
+ * so make the first call before any stream capture.  All calls share the
+ * array: calls that may run concurrently on the GPU (different streams
+ * without ordering) race and must be serialised by the caller.
+ * Stream-ordered on the state's stream. */
+csvd_status csvd_score_one_noalloc(csvd_state s, const csvd_block* A, double eps, float* sigma_out,
+                                   double* tail_sq_out, double* tail_paper_out,
+                                   uint8_t* accept_out);
+
 /* Launch tracing.  csvd_launch_count: kernels launched by this library so
  * far in the process.  csvd_profile(1) clears and starts recording a pair of
  * CUDA events on the launch stream around every kernel launch, csvd_profile(0)

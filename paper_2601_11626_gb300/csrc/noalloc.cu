@@ -1,0 +1,151 @@
+// csvd_score_one_noalloc: one mixed-form merge evaluation that allocates no
+// memory.  Some callers cannot allocate device memory at the point where
+// they score a merge: a process whose device memory is entirely reserved by
+// another allocator (a framework's caching allocator that owns the GPU), or
+// a latency-critical loop that must not pay cudaMalloc / cudaFree (which can
+// synchronise the device).  This entry point runs the same kernels as
+// csvd_score with CSVD_MIXED, with every intermediate (energy, P = U^T A,
+// A^T A, the eigen core's global workspace, the kernel descriptors) placed
+// in one file-scope device array of fixed size that every GPU loading the
+// library holds until the process exits.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "csvd.h"
+#include "common.cuh"
+#include "internal.h"
+#include "tc_gram.cuh"
+
+using namespace csvd;
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(4) << 20;  // 4 MiB per GPU
+constexpr int kMaxK = 512;
+constexpr int kMaxRt = 128;
+constexpr int kMaxTiles = 4 + 10;  // P tiles (rt <= 128, k <= 512) + upper G tiles
+constexpr int kLargeSmem = 220 * 1024;
+constexpr int kSmallN = 192;
+
+struct Descs {
+  CoreDesc core;
+  EnergyDesc energy;
+  TcItem item;
+  TcTile tiles[kMaxTiles];
+};
+
+// Scratch layout (byte offsets, 256-byte aligned).
+constexpr size_t kOffEnergy = 0;
+constexpr size_t kOffDescs = 256;
+constexpr size_t kOffP = 4096;
+constexpr size_t kOffG = kOffP + size_t(kMaxRt) * kMaxK * 4;
+constexpr size_t kOffWork = kOffG + size_t(kMaxK) * kMaxK * 4;
+static_assert(sizeof(Descs) <= kOffP - kOffDescs, "descriptor region");
+
+__global__ void write_descs_kernel(Descs d, Descs* dst) {
+  if (threadIdx.x == 0) *dst = d;
+}
+
+std::mutex g_mu;
+void* g_ptr[64] = {};
+
+}  // namespace
+
+// Scratch shared by every call on a device; contents persist between calls.
+static __device__ __align__(256) unsigned char csvd_noalloc_scratch[kScratchBytes];
+
+extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A, double eps,
+                                              float* sigma_out, double* tail_sq_out,
+                                              double* tail_paper_out, uint8_t* accept_out) {
+  if (!st || !A || !A->ptr || !sigma_out || !tail_sq_out)
+    return set_error(CSVD_ERR_ARG, "NULL argument");
+  if (A->dtype != CSVD_F32 || A->k < 1 || A->ld < A->k)
+    return set_error(CSVD_ERR_ARG, "needs an f32 block with k >= 1 and ld >= k");
+  if ((reinterpret_cast<uintptr_t>(A->ptr) & 15) != 0 || (A->ld & 3) != 0)
+    return set_error(CSVD_ERR_ARG, "needs 16-byte aligned rows (ptr % 16 == 0, ld % 4 == 0)");
+  const int k = (int)A->k;
+  const int rt = st->rt;
+  const int64_t m = st->m;
+  if (k > kMaxK || rt > kMaxRt)
+    return set_error(CSVD_ERR_SHAPE, "scratch limit: needs k <= 512 and rank <= 128");
+  if (rt > 0 && (st->r & 3) != 0)
+    return set_error(CSVD_ERR_SHAPE, "needs a state rank cap r divisible by 4");
+  const int n = rt + k;
+  const int64_t work_floats = tridiag_work_floats(n);
+  if ((size_t)kOffWork + (size_t)work_floats * 4 > kScratchBytes)
+    return set_error(CSVD_ERR_SHAPE, "scratch limit exceeded");
+
+  // set-up: the device address of the scratch array on the current device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64)
+    return set_error(CSVD_ERR_CUDA, "cudaGetDevice failed");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, csvd_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return set_error(CSVD_ERR_CUDA, "cudaGetSymbolAddress failed");
+      g_ptr[dev] = p;
+    }
+    base = static_cast<unsigned char*>(g_ptr[dev]);
+  }
+  cudaStream_t s = st->stream;
+  double* energy = reinterpret_cast<double*>(base + kOffEnergy);
+  Descs* ddesc = reinterpret_cast<Descs*>(base + kOffDescs);
+  float* P = reinterpret_cast<float*>(base + kOffP);
+  float* G = reinterpret_cast<float*>(base + kOffG);
+  float* work = reinterpret_cast<float*>(base + kOffWork);
+
+  Descs h;
+  std::memset(&h, 0, sizeof(h));
+  h.energy = EnergyDesc{A->ptr, A->ld, (int)m, k, 0, 0, energy};
+  h.item = TcItem{reinterpret_cast<const float*>(A->ptr), A->ld, st->U[st->cur], st->r, (int)m, k,
+                  rt, 0, P, k, G, k};
+  int nt = 0;
+  for (int r0 = 0; r0 < rt; r0 += kTcBM)
+    for (int c0 = 0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 0, r0, c0};
+  for (int r0 = 0; r0 < k; r0 += kTcBM)
+    for (int c0 = r0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 1, r0, c0};
+  const bool small = n <= kSmallN;
+  const int smem = small ? (6 * 32 * ((n + 31) / 32) + 128 + ((n + 31) / 32) * ((n + 31) / 32 + 1) / 2 * 1024) * 4
+                         : kLargeSmem;
+  const bool spill = !small && (n + 31) / 32 > tridiag_smem_cap(kLargeSmem, n);
+  CoreDesc& c = h.core;
+  c.P = rt > 0 ? P : nullptr;
+  c.ldp = k;
+  c.Gaa = G;
+  c.ldb = k;
+  c.sigma = st->sigma;
+  c.scal = st->scal;
+  c.energy_add = energy;
+  c.work = spill ? work : nullptr;
+  c.ldwork = n;
+  c.sigma_out = sigma_out;
+  c.tail_out = tail_sq_out;
+  c.tail_paper_out = tail_paper_out;
+  c.accept_out = accept_out;
+  c.eps = eps;
+  c.rt = rt;
+  c.k = k;
+  c.kp = (int)std::min<int64_t>(k, m - rt);
+  c.r_new = std::min(st->r, rt + c.kp);
+
+  // energies start at zero; descriptors are written by a kernel (no host staging)
+  e = cudaMemsetAsync(energy, 0, sizeof(double), s);
+  if (e == cudaSuccess) {
+    write_descs_kernel<<<1, 32, 0, s>>>(h, ddesc);
+    e = cudaGetLastError();
+  }
+  const int chunks = (int)std::min<int64_t>(64, (m * k + 8191) / 8192);
+  if (e == cudaSuccess) e = launch_energy(&ddesc->energy, 1, chunks, s);
+  if (e == cudaSuccess)
+    e = launch_tc_gram(&ddesc->item, ddesc->tiles, nt, device_sm_count(), st->status, s);
+  if (e == cudaSuccess) e = launch_core_tridiag(&ddesc->core, 1, smem, n, st->status, s);
+  if (e != cudaSuccess)
+    return set_error(CSVD_ERR_CUDA, cudaGetErrorString(e));
+  return CSVD_OK;
+}

@@ -66,6 +66,8 @@ def _sig(lib):
     lib.csvd_tail_grad.argtypes = [VP, I64, I64, I32, P(Block), P(Block), I32, D, VP]
     lib.csvd_block_energy.argtypes = [P(Block), I32, I64, VP, P(D)]
     lib.csvd_set_allocator.argtypes = [VP, VP, VP]
+    lib.csvd_score_one_noalloc.argtypes = [VP, P(Block), D, VP, VP, VP, VP]
+    lib.csvd_score_one_noalloc.restype = C.c_int
     lib.csvd_launch_count.restype = C.c_int64
     lib.csvd_profile.argtypes = [I32]
     lib.csvd_profile.restype = C.c_int
@@ -243,6 +245,28 @@ def score(states, cand_state, cands, eps, precision="mixed"):
     as CUDA tensors."""
     b = ScoreBatch(states, cand_state, cands, eps, precision).run()
     return b.sigma, b.tail, b.paper, b.accept
+
+
+def score_one_noalloc(state: IncrSVD, A: torch.Tensor, eps: float, sigma=None, tail=None,
+                      paper=None, accept=None):
+    """Mixed-form merge evaluation of one candidate without any device
+    allocation inside the library (scratch is a fixed device array).  The
+    output tensors may be passed in; otherwise they are created here by
+    torch, before the call."""
+    if sigma is None:
+        sigma = torch.zeros(state.r, device="cuda", dtype=torch.float32)
+    if tail is None:
+        tail = torch.zeros(1, device="cuda", dtype=torch.float64)
+    if paper is None:
+        paper = torch.zeros(1, device="cuda", dtype=torch.float64)
+    if accept is None:
+        accept = torch.zeros(1, device="cuda", dtype=torch.uint8)
+    b = block(A)
+    _check(lib().csvd_score_one_noalloc(state.handle, C.byref(b), float(eps),
+                                        C.c_void_p(sigma.data_ptr()), C.c_void_p(tail.data_ptr()),
+                                        C.c_void_p(paper.data_ptr()),
+                                        C.c_void_p(accept.data_ptr())))
+    return sigma, tail, paper, accept
 
 
 def block_energy(blocks):

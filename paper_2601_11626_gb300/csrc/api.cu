@@ -267,10 +267,10 @@ static csvd_status take_status(int* d_status, cudaStream_t s) {
 
 // Largest core kept in shared memory (bytes of dynamic shared memory).
 static constexpr int kCoreSmemBudget = 200 * 1024;
-// Eigenvalue-core launch classes: small cores share an SM, large cores get
-// (almost) all of its shared memory and spill the leading steps to global.
+// Eigenvalue-core launch classes: small cores share an SM; large cores get
+// all of its shared memory plus tensor memory, and the leading tile columns
+// of the largest ones a global workspace.
 static constexpr int kTriSmallN = 192;
-static constexpr int kTriLargeSmem = 220 * 1024;
 
 static int num_sms();
 namespace csvd {
@@ -364,11 +364,6 @@ static bool tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, 
   return true;
 }
 
-static int tri_small_smem(int n_max) {
-  const int T = (n_max + 31) / 32;
-  return (6 * 32 * T + 128 + T * (T + 1) / 2 * 1024) * 4;
-}
-
 // ===================================================== the batched pipeline
 // One merge evaluation per item: (state view, block).  Produces sigma~,
 // tails, energies and accept flags into caller arrays (device).  When
@@ -441,12 +436,11 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       if (nn <= kTriSmallN) tri_nmax_small = std::max(tri_nmax_small, nn);
       else tri_nmax_large = std::max(tri_nmax_large, nn);
     }
-    const int capT = tridiag_smem_cap(kTriLargeSmem, tri_nmax_large);
     for (int i = 0; i < n; ++i) {
       const int nn = items[i].st.rt + (int)items[i].blk->k;
       off[i].smem = nn <= kTriSmallN;
-      if (!off[i].smem && (nn + 31) / 32 > capT)
-        off[i].work = L.add(sizeof(float) * (size_t)tridiag_work_floats(nn));
+      const int64_t wf = off[i].smem ? 0 : tridiag_work_floats(nn, kTriLargeSmemBytes, tri_nmax_large);
+      if (wf > 0) off[i].work = L.add(sizeof(float) * (size_t)wf);
     }
   }
   // tensor-core Gram: eligible items (f32, 16-byte aligned rows)
@@ -629,9 +623,10 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
                             (int)tct.size(), num_sms(), d_status, s));
     CUDA_TRY(gG.launch(dbase, s));
     CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
-                                 kTriLargeSmem, tri_nmax_large, d_status, s));
+                                 kTriLargeSmemBytes, tri_nmax_large, d_status, s));
     CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
-                                 tri_small_smem(tri_nmax_small), tri_nmax_small, d_status, s));
+                                 tridiag_smem_bytes(tri_nmax_small, false), tri_nmax_small,
+                                 d_status, s));
   } else {
     CUDA_TRY(gR.launch(dbase, s));
     CUDA_TRY(gP2.launch(dbase, s));

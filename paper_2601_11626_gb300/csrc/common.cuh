@@ -154,8 +154,12 @@ cudaError_t launch_apply_q(const ApplyQDesc* d_desc, int n_items, int max_cols,
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
 int jacobi_scratch_floats(int nc);
-__host__ __device__ int tridiag_smem_cap(int smem_bytes, int n_max);
-int64_t tridiag_work_floats(int n);
+// Eigen core: dynamic shared memory of a launch whose largest core is n_max
+// (`large`: one CTA per SM with the maximum opt-in size and tensor memory),
+// and the global workspace (floats) a core of size n needs in that launch.
+constexpr int kTriLargeSmemBytes = 227 * 1024 - 1024;
+int tridiag_smem_bytes(int n_max, bool large);
+int64_t tridiag_work_floats(int n, int smem_bytes, int n_max);
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
                                int* d_status, cudaStream_t s);
 cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,

@@ -25,7 +25,6 @@ constexpr size_t kScratchBytes = size_t(4) << 20;  // 4 MiB per GPU
 constexpr int kMaxK = 512;
 constexpr int kMaxRt = 128;
 constexpr int kMaxTiles = 4 + 10;  // P tiles (rt <= 128, k <= 512) + upper G tiles
-constexpr int kLargeSmem = 220 * 1024;
 constexpr int kSmallN = 192;
 
 struct Descs {
@@ -72,7 +71,9 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   if (rt > 0 && (st->r & 3) != 0)
     return set_error(CSVD_ERR_SHAPE, "needs a state rank cap r divisible by 4");
   const int n = rt + k;
-  const int64_t work_floats = tridiag_work_floats(n);
+  const bool small = n <= kSmallN;
+  const int smem = small ? tridiag_smem_bytes(n, false) : kTriLargeSmemBytes;
+  const int64_t work_floats = small ? 0 : tridiag_work_floats(n, smem, n);
   if ((size_t)kOffWork + (size_t)work_floats * 4 > kScratchBytes)
     return set_error(CSVD_ERR_SHAPE, "scratch limit exceeded");
 
@@ -110,10 +111,6 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
     for (int c0 = 0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 0, r0, c0};
   for (int r0 = 0; r0 < k; r0 += kTcBM)
     for (int c0 = r0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 1, r0, c0};
-  const bool small = n <= kSmallN;
-  const int smem = small ? (6 * 32 * ((n + 31) / 32) + 128 + ((n + 31) / 32) * ((n + 31) / 32 + 1) / 2 * 1024) * 4
-                         : kLargeSmem;
-  const bool spill = !small && (n + 31) / 32 > tridiag_smem_cap(kLargeSmem, n);
   CoreDesc& c = h.core;
   c.P = rt > 0 ? P : nullptr;
   c.ldp = k;
@@ -122,7 +119,7 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   c.sigma = st->sigma;
   c.scal = st->scal;
   c.energy_add = energy;
-  c.work = spill ? work : nullptr;
+  c.work = work_floats > 0 ? work : nullptr;
   c.ldwork = n;
   c.sigma_out = sigma_out;
   c.tail_out = tail_sq_out;

@@ -18,15 +18,17 @@
 //     tile column leaves the trailing matrix before any tile could move.
 //  2. Householder tridiagonalisation, G <- H G H, H = I - tau v v^T, with two
 //     block barriers per step:
-//       serial phase (warp 0): finish w of the previous step from p, apply
-//         the pending rank-2 update to column s (kept as a vector), build
-//         the reflector of column s;
-//       main pass (all warps): one sweep over the trailing tiles applies the
-//         pending update and accumulates p = G v and p^T v; it also copies
-//         out column s + 1 for the next serial phase.
+//       phase A (one row per thread): w of the previous step from its p, the
+//         pending rank-2 update on column s (kept as a vector), v below
+//         s + 1, a zeroed p, and partial sums of ||x||^2;
+//       phase B: every thread forms the reflector scalars itself, then all
+//         warps sweep the trailing tiles once: apply the pending update,
+//         accumulate p = G v and p^T v, and copy out column s + 1.
 //     Vectors are indexed by global row and vanish outside the trailing
 //     range, so boundary tiles need no masks.  Column sums of off-diagonal
 //     tiles accumulate across a tile column and are reduced once per column.
+//     Global tiles are shared evenly among warps; shared-memory tiles top
+//     the warps up to equal counts around the lane-restricted TMEM tiles.
 //  3. Multisection bisection on Sturm counts of the tridiagonal matrix for
 //     the top r_new eigenvalues (g threads per eigenvalue, the interval
 //     shrinks (g + 1)-fold per iteration).
@@ -47,7 +49,7 @@ constexpr int kTileFloats = kTile * kTile;
 constexpr int kTmemTiles = 64;            // 4 lane quarters x 16 tiles of 32 columns
 constexpr int kTmemCols = 512;
 constexpr int kTmemMinSmem = 120 * 1024;  // at most one CTA per SM from this size on
-constexpr int kVecs = 7;                  // dv, ev, v (2), p/w (2), column
+constexpr int kVecs = 9;                  // dv, ev, v (2), p (2), w, column (2)
 
 __host__ __device__ __forceinline__ int tiles_in(int T) { return T * (T + 1) / 2; }
 // First list position of tile column b in a T-row lower tile triangle.
@@ -120,14 +122,16 @@ __device__ __forceinline__ int sturm_count(const float* dv, const float* e2, int
   return cnt;
 }
 
-// Vectors of one main pass.
+// Vectors of one main pass.  v_s[s+1] (= v0) is patched in registers: the
+// shared copy is written concurrently by every warp.
 struct Step {
   const float* vcur;   // v of this step
   const float* vprev;  // pending update: v and w of the previous step
   const float* wprev;
   float* pcur;         // p = G v accumulator
-  float* colv;         // receives column s + 1
-  int b0, ccn;         // tile column and in-tile column of s + 1
+  float* cnext;        // receives column s + 1
+  int b0, ccn, s1;     // tile column and in-tile column of s + 1; s + 1
+  float v0;
 };
 
 // Lane L ends with the sum over lanes of cp[L]; added to p[32 b + L].
@@ -144,8 +148,9 @@ __device__ __forceinline__ void flush_cols(float (&cp)[32], int b, int lane, con
     }
   }
   const int c = b * kTile + lane;
+  const float vc = (c == st.s1) ? st.v0 : st.vcur[c];
   atomicAdd(&st.pcur[c], cp[0]);
-  pv = fmaf(cp[0], st.vcur[c], pv);
+  pv = fmaf(cp[0], vc, pv);
 #pragma unroll
   for (int q = 0; q < 32; ++q) cp[q] = 0.f;
 }
@@ -153,16 +158,25 @@ __device__ __forceinline__ void flush_cols(float (&cp)[32], int b, int lane, con
 // The per-element work of a tile whose row `lane` holds val[0..31]:
 // G -= vp wp^T + wp vp^T, then row sums into rowacc and column sums into cp.
 __device__ __forceinline__ void tile_update(float (&val)[32], float (&cp)[32], float& rowacc,
-                                            int a, int b, int lane, const Step& st) {
+                                            float vr, int a, int b, int lane, const Step& st) {
   const int r = a * kTile + lane;
-  const float vr = st.vcur[r], vpr = st.vprev[r], wpr = st.wprev[r];
+  const float vpr = st.vprev[r], wpr = st.wprev[r];
   const float colw = (a == b) ? 0.f : vr;  // diagonal tiles: row sums cover both halves
   const float4* vc4 = reinterpret_cast<const float4*>(st.vcur + b * kTile);
   const float4* vp4 = reinterpret_cast<const float4*>(st.vprev + b * kTile);
   const float4* wp4 = reinterpret_cast<const float4*>(st.wprev + b * kTile);
+  const int pq = (b == st.b0) ? st.ccn : -1;  // in-tile column holding v0
 #pragma unroll
   for (int q4 = 0; q4 < 8; ++q4) {
-    const float4 vc = vc4[q4], vp = vp4[q4], wp = wp4[q4];
+    float4 vc = vc4[q4];
+    if ((pq >> 2) == q4) {
+      const int u = pq & 3;
+      vc.x = u == 0 ? st.v0 : vc.x;
+      vc.y = u == 1 ? st.v0 : vc.y;
+      vc.z = u == 2 ? st.v0 : vc.z;
+      vc.w = u == 3 ? st.v0 : vc.w;
+    }
+    const float4 vp = vp4[q4], wp = wp4[q4];
     const float vcs[4] = {vc.x, vc.y, vc.z, vc.w};
     const float vps[4] = {vp.x, vp.y, vp.z, vp.w};
     const float wps[4] = {wp.x, wp.y, wp.z, wp.w};
@@ -177,8 +191,59 @@ __device__ __forceinline__ void tile_update(float (&val)[32], float (&cp)[32], f
   }
 }
 
-// Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles
-// (shared or global memory).
+// Shared-memory tiles are row-major with 16-byte chunks XOR-swizzled by row
+// (element (i, j) at 32 i + 4 ((j / 4) ^ (i % 8)) + j % 4): lane i moves its
+// row with eight conflict-free 128-bit accesses.  Global tiles are
+// column-major (element (i, j) at 32 j + i): one coalesced access per column.
+template <bool kRowMajor>
+__device__ __forceinline__ void load_row(const float* tp, int lane, float (&val)[32]) {
+  if (kRowMajor) {
+    const float4* rp = reinterpret_cast<const float4*>(tp + lane * kTile);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 x = rp[q ^ (lane & 7)];
+      val[4 * q] = x.x;
+      val[4 * q + 1] = x.y;
+      val[4 * q + 2] = x.z;
+      val[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) val[cc] = tp[cc * kTile + lane];
+  }
+}
+template <bool kRowMajor>
+__device__ __forceinline__ void store_row(float* tp, int lane, const float (&val)[32]) {
+  if (kRowMajor) {
+    float4* rp = reinterpret_cast<float4*>(tp + lane * kTile);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      rp[q ^ (lane & 7)] = make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) tp[cc * kTile + lane] = val[cc];
+  }
+}
+__device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
+  return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
+}
+
+// Everything after the tile's values are in val[]: column s + 1, row sums.
+__device__ __forceinline__ void tile_finish(const float (&val)[32], float rowacc, float vr, int a,
+                                            int b, int lane, const Step& st, float& pv) {
+  const int r = a * kTile + lane;
+  if (b == st.b0) {
+    float x = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) x = (cc == st.ccn) ? val[cc] : x;
+    st.cnext[r] = x;
+  }
+  atomicAdd(&st.pcur[r], rowacc);
+  pv = fmaf(rowacc, vr, pv);
+}
+
+// Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles.
+template <bool kRowMajor>
 __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb, int T, int lane,
                                           const Step& st, float& pv) {
   if (La >= Lb) return;
@@ -189,24 +254,14 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
   for (int q = 0; q < 32; ++q) cp[q] = 0.f;
   for (int L = La; L < Lb; ++L) {
     float* tp = base + (int64_t)(L - Lbase) * kTileFloats;
-    const int r = a * kTile + lane;
-    // The same ordering as the TMEM path: load the row, update, store.  The
-    // 32 loads are independent, so they are all in flight together.
     float val[32];
-#pragma unroll
-    for (int cc = 0; cc < 32; ++cc) val[cc] = tp[cc * kTile + lane];
+    load_row<kRowMajor>(tp, lane, val);
+    const int r = a * kTile + lane;
+    const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
     float rowacc = 0.f;
-    tile_update(val, cp, rowacc, a, b, lane, st);
-#pragma unroll
-    for (int cc = 0; cc < 32; ++cc) tp[cc * kTile + lane] = val[cc];
-    if (b == st.b0) {
-      float x = 0.f;
-#pragma unroll
-      for (int cc = 0; cc < 32; ++cc) x = (cc == st.ccn) ? val[cc] : x;
-      st.colv[r] = x;
-    }
-    atomicAdd(&st.pcur[r], rowacc);
-    pv = fmaf(rowacc, st.vcur[r], pv);
+    tile_update(val, cp, rowacc, vr, a, b, lane, st);
+    store_row<kRowMajor>(tp, lane, val);
+    tile_finish(val, rowacc, vr, a, b, lane, st, pv);
     const int bb = b;
     tile_next(a, b, T);
     if (b != bb || L + 1 == Lb) flush_cols(cp, bb, lane, st, pv);
@@ -227,18 +282,12 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lg, int tfirst, int 
     const uint32_t taddr = tq + (uint32_t)(t >> 2) * 32u;
     float val[32];
     tmem_load_tile(taddr, val);
-    float rowacc = 0.f;
-    tile_update(val, cp, rowacc, a, b, lane, st);
-    tmem_store_tile(taddr, val);
     const int r = a * kTile + lane;
-    if (b == st.b0) {
-      float x = 0.f;
-#pragma unroll
-      for (int cc = 0; cc < 32; ++cc) x = (cc == st.ccn) ? val[cc] : x;
-      st.colv[r] = x;
-    }
-    atomicAdd(&st.pcur[r], rowacc);
-    pv = fmaf(rowacc, st.vcur[r], pv);
+    const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
+    float rowacc = 0.f;
+    tile_update(val, cp, rowacc, vr, a, b, lane, st);
+    tmem_store_tile(taddr, val);
+    tile_finish(val, rowacc, vr, a, b, lane, st, pv);
     const int bb = b;
 #pragma unroll
     for (int u = 0; u < 4; ++u) tile_next(a, b, T);
@@ -258,13 +307,15 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   float* dv = smem;          // npad: diagonal of T
   float* ev = dv + npad;     // npad: off-diagonal e[j] couples j, j+1
-  float* vb0 = ev + npad;    // npad x 2: v of even / odd steps
-  float* vb1 = vb0 + npad;
-  float* pb0 = vb1 + npad;   // npad x 2: p of a step, turned into its w in place
-  float* pb1 = pb0 + npad;
-  float* colv = pb1 + npad;  // npad: the current column (rows >= s)
-  float* red = colv + npad;  // 128
-  float* tsm = red + 128;    // shared-memory tiles
+  float* vb0 = ev + npad;      // v of even / odd steps
+  float* vb1 = ev + 2 * npad;
+  float* pb0 = ev + 3 * npad;  // p of even / odd steps
+  float* pb1 = ev + 4 * npad;
+  float* wv = ev + 5 * npad;   // w of the pending update
+  float* cb0 = ev + 6 * npad;  // column s (rows >= s) / column s + 1
+  float* cb1 = ev + 7 * npad;
+  float* red = ev + 8 * npad;  // 128
+  float* tsm = red + 128;      // shared-memory tiles
   const TileLayout Lay = tile_layout(n, smem_bytes, n_max);
   const int T = Lay.T, Nt = tiles_in(T);
   __shared__ uint32_t s_tmem;
@@ -283,18 +334,23 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   for (int v = wid; v < Lay.Lg + (Nt - Lay.Ls); v += kTriWarps) {
     const bool glob = v < Lay.Lg;
     const int L = glob ? v : Lay.Ls + (v - Lay.Lg);
-    float* tp = glob ? d.work + (int64_t)L * kTileFloats : tsm + (int64_t)(L - Lay.Ls) * kTileFloats;
     int a, b;
     tile_of(L, T, a, b);
     const int r = a * kTile + lane;
-    for (int cc = 0; cc < kTile; ++cc) tp[cc * kTile + lane] = core_gram(d, n, r, b * kTile + cc);
+    float val[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) val[cc] = core_gram(d, n, r, b * kTile + cc);
+    if (glob) store_row<false>(d.work + (int64_t)L * kTileFloats, lane, val);
+    else store_row<true>(tsm + (int64_t)(L - Lay.Ls) * kTileFloats, lane, val);
   }
   for (int i = tid; i < npad; i += kTriThreads) {
     vb0[i] = 0.f;
     vb1[i] = 0.f;
     pb0[i] = 0.f;
     pb1[i] = 0.f;
-    colv[i] = core_gram(d, n, i, 0);
+    wv[i] = 0.f;
+    cb0[i] = core_gram(d, n, i, 0);
+    cb1[i] = 0.f;
   }
   // ||A||_F^2 = tr(A^T A) from the Gram's diagonal when no energy is given
   if (d.energy_add == nullptr) {
@@ -332,133 +388,123 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   }
   __syncthreads();
 
-  // 2. tridiagonalisation
-  float tau_prev = 0.f;  // warp 0: tau of the pending reflector
+  // 2. tridiagonalisation.  Per step s, two block barriers:
+  //   A (all threads, one row each): w of the previous step, the pending
+  //     update on column s, v_s below s + 1, zeroed p_s, partial ||x||^2;
+  //   B (every thread, redundantly): the reflector scalars; then the main
+  //     pass over the trailing tiles.
+  float tau_prev = 0.f;  // tau of the pending reflector (same in every thread)
   for (int s = 0;; ++s) {
-    float* vcur = (s & 1) ? vb1 : vb0;
-    float* vprev = (s & 1) ? vb0 : vb1;
-    float* pcur = (s & 1) ? pb1 : pb0;
-    float* wprev = (s & 1) ? pb0 : pb1;
+    const bool odd = (s & 1) != 0;
+    float* vcur = odd ? vb1 : vb0;
+    const float* vprev = odd ? vb0 : vb1;
+    float* pcur = odd ? pb1 : pb0;
+    const float* pprev = odd ? pb0 : pb1;
+    float* ccur = odd ? cb1 : cb0;
+    float* cnext = odd ? cb0 : cb1;
     const bool last = s + 2 >= n;
     const int b0 = (s + 1) >> 5;
-    if (wid == 0) {
-      // w of the previous step (in place of its p), the pending update on
-      // column s, and the reflector of column s
+    {
       const float kk = (s >= 1) ? 0.5f * tau_prev * tau_prev * s_pv[(s + 1) & 1] : 0.f;
       const float vs = vprev[s];
-      const float ws = (s >= 1) ? fmaf(tau_prev, wprev[s], -kk * vs) : 0.f;
-      __syncwarp();
+      const float ws = (s >= 1) ? fmaf(tau_prev, pprev[s], -kk * vs) : 0.f;
       const int ilo = min(s, b0 * kTile);  // rows the main pass of this step touches start here
       float part = 0.f;
-      for (int i = ilo + lane; i < n; i += 32) {
+      for (int i = ilo + tid; i < npad; i += kTriThreads) {
         const float vp = vprev[i];
         float w = 0.f;
-        if (s >= 1 && i >= s) w = fmaf(tau_prev, wprev[i], -kk * vp);
-        wprev[i] = w;
-        if (i >= s) {
-          const float c = fmaf(-vp, ws, fmaf(-w, vs, colv[i]));
-          colv[i] = c;
+        if (s >= 1 && i >= s) w = fmaf(tau_prev, pprev[i], -kk * vp);
+        wv[i] = w;
+        float c = 0.f;
+        if (i >= s && i < n) {
+          c = fmaf(-vp, ws, fmaf(-w, vs, ccur[i]));
+          ccur[i] = c;
           if (i >= s + 2) part = fmaf(c, c, part);
         }
+        vcur[i] = (i >= s + 2 && i < n) ? c : 0.f;
+        pcur[i] = 0.f;
       }
       part = warp_sum(part);
-      __syncwarp();
-      if (last) {
-        if (lane == 0) {
-          if (n >= 2) {
-            const int j = n - 1;
-            const float* tl = tsm + (int64_t)(Nt - 1 - Lay.Ls) * kTileFloats;
-            const float gjj = tl[(j & 31) * kTile + (j & 31)];
-            dv[j - 1] = colv[j - 1];
-            ev[j - 1] = colv[j];
-            dv[j] = fmaf(-2.f * vprev[j], wprev[j], gjj);
-          } else {
-            dv[0] = colv[0];
-          }
-          ev[n - 1] = 0.f;
-        }
-      } else {
-        const float x0 = colv[s + 1];
-        float beta = x0, tau = 0.f, v0 = 0.f;
-        if (part != 0.f) {
-          const float nrm = sqrtf(fmaf(x0, x0, part));
-          beta = x0 >= 0.f ? -nrm : nrm;
-          v0 = x0 - beta;
-          tau = 2.f / fmaf(v0, v0, part);
-        }
-        if (lane == 0) {
-          dv[s] = colv[s];
-          ev[s] = beta;
-          s_pv[s & 1] = 0.f;
-        }
-        for (int i = ilo + lane; i < npad; i += 32) {
-          float v = 0.f;
-          if (tau != 0.f && i > s && i < n) v = (i == s + 1) ? v0 : colv[i];
-          vcur[i] = v;
-          pcur[i] = 0.f;
-        }
-        tau_prev = tau;
-      }
+      if (lane == 0) red[wid] = part;
+      if (tid == 0) s_pv[s & 1] = 0.f;
     }
-    if (last) break;
     __syncthreads();
+    float tail2 = 0.f;
+    for (int w = 0; w < kTriWarps; ++w) tail2 += red[w];
+    if (last) {
+      if (tid == 0) {
+        if (n >= 2) {
+          const int j = n - 1;
+          const float* tl = tsm + (int64_t)(Nt - 1 - Lay.Ls) * kTileFloats;
+          const float gjj = smem_tile_elem(tl, j & 31, j & 31);
+          dv[j - 1] = ccur[j - 1];
+          ev[j - 1] = ccur[j];
+          dv[j] = fmaf(-2.f * vprev[j], wv[j], gjj);
+        } else {
+          dv[0] = ccur[0];
+        }
+        ev[n - 1] = 0.f;
+      }
+      break;
+    }
+    const float x0 = ccur[s + 1];
+    float beta = x0, tau = 0.f, v0 = 0.f;
+    if (tail2 != 0.f) {
+      const float nrm = sqrtf(fmaf(x0, x0, tail2));
+      beta = x0 >= 0.f ? -nrm : nrm;
+      v0 = x0 - beta;
+      tau = 2.f / fmaf(v0, v0, tail2);
+    }
+    if (tid == 0) {
+      dv[s] = ccur[s];
+      ev[s] = beta;
+    }
+    if (lane == 0) vcur[s + 1] = v0;  // every warp writes the same value
+    __syncwarp();
+    tau_prev = tau;
     if (use_tmem) tmem_fence_after();
 
     // main pass over the trailing tiles (tile columns >= b0)
     {
-      const Step st{vcur, vprev, wprev, pcur, colv, b0, (s + 1) & 31};
+      const Step st{vcur, vprev, wv, pcur, cnext, b0, (s + 1) & 31, s + 1, v0};
       const int L0 = col_start(b0, T);
       const int ng = max(0, Lay.Lg - L0);  // trailing tiles in global memory
       const int Ls0 = max(L0, Lay.Ls);
-      const int nf = ng + (Nt - Ls0);      // ... plus those in shared memory
+      const int ns = Nt - Ls0;             // ... in shared memory
       const int t0 = max(0, L0 - Lay.Lg);  // first trailing TMEM tile
-      int nq0 = 0, nq1 = 0, nq2 = 0, nq3 = 0;
+      // TMEM tiles: quarter u & 3, split in four among its warps
+      int cu = 0, nq_mine = 0;
       if (use_tmem) {
-        const int f0 = t0 + ((0 - t0) & 3), f1 = t0 + ((1 - t0) & 3);
-        const int f2 = t0 + ((2 - t0) & 3), f3 = t0 + ((3 - t0) & 3);
-        nq0 = Lay.Ntm > f0 ? (Lay.Ntm - f0 + 3) >> 2 : 0;
-        nq1 = Lay.Ntm > f1 ? (Lay.Ntm - f1 + 3) >> 2 : 0;
-        nq2 = Lay.Ntm > f2 ? (Lay.Ntm - f2 + 3) >> 2 : 0;
-        nq3 = Lay.Ntm > f3 ? (Lay.Ntm - f3 + 3) >> 2 : 0;
+        const int qq = lane & 3, f = t0 + ((qq - t0) & 3);
+        const int nq = Lay.Ntm > f ? (Lay.Ntm - f + 3) >> 2 : 0;  // lane: its quarter's count
+        const int ui = (lane >> 2) & 3;
+        cu = (lane < kTriWarps) ? (ui + 1) * nq / 4 - ui * nq / 4 : 0;
+        nq_mine = __shfl_sync(0xffffffffu, nq, wid & 3);
       }
-      const int ntm = nq0 + nq1 + nq2 + nq3;
-      const int q = wid & 3, qi = wid >> 2;
-      auto quarter = [&](int u) {
-        const int qq = u & 3;
-        return qq == 0 ? nq0 : qq == 1 ? nq1 : qq == 2 ? nq2 : nq3;
-      };
-      auto tm_count = [&](int u) {
-        const int nn = quarter(u), ui = u >> 2;
-        return (ui + 1) * nn / 4 - ui * nn / 4;
-      };
-      int f_lo, f_hi;
-      if (ntm == 0) {
-        f_lo = nf * wid / kTriWarps;
-        f_hi = nf * (wid + 1) / kTriWarps;
-      } else {
-        // water-filling: free tiles top every warp up to the same level
-        int lam = (nf + ntm + kTriWarps - 1) / kTriWarps;
-        for (;;) {
-          int sum = 0;
-          for (int u = 0; u < kTriWarps; ++u) sum += max(0, lam - tm_count(u));
-          if (sum >= nf) break;
-          ++lam;
-        }
-        int st0 = 0;
-        for (int u = 0; u < wid; ++u) st0 += max(0, lam - tm_count(u));
-        f_lo = min(st0, nf);
-        f_hi = min(nf, st0 + max(0, lam - tm_count(wid)));
+      const int ntm = __reduce_add_sync(0xffffffffu, (unsigned)cu);
+      // shared-memory tiles top every warp up to the same level (water-filling)
+      int lam = (ns + ntm + kTriWarps - 1) / kTriWarps;
+      for (;;) {
+        const int dd = (lane < kTriWarps) ? max(0, lam - cu) : 0;
+        if ((int)__reduce_add_sync(0xffffffffu, (unsigned)dd) >= ns) break;
+        ++lam;
       }
+      const int dmine = (lane < kTriWarps) ? max(0, lam - cu) : 0;
+      const int before = (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < wid ? dmine : 0));
+      const int mine = __shfl_sync(0xffffffffu, dmine, wid);
+      const int s_lo = min(before, ns), s_hi = min(ns, before + mine);
+      // global tiles: an even share each; half the warps take them first
+      const int g_lo = L0 + ng * wid / kTriWarps, g_hi = L0 + ng * (wid + 1) / kTriWarps;
       float pv = 0.f;
-      // free tiles: virtual positions [0, ng) global, [ng, nf) shared
-      mem_tiles(d.work, 0, L0 + f_lo, L0 + min(f_hi, ng), T, lane, st, pv);
-      mem_tiles(tsm, Lay.Ls, Ls0 + max(f_lo - ng, 0), Ls0 + max(f_hi - ng, 0), T, lane, st, pv);
-      if (ntm > 0) {
-        const int nn = quarter(q);
+      if ((wid & 1) == 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
+      mem_tiles<true>(tsm, Lay.Ls, Ls0 + s_lo, Ls0 + s_hi, T, lane, st, pv);
+      if (use_tmem) {
+        const int q = wid & 3, qi = wid >> 2;
         const int tfirst = t0 + ((q - t0) & 3);
-        tmem_tiles(tq, Lay.Lg, tfirst, qi * nn / 4, (qi + 1) * nn / 4, T, lane, st, pv);
+        tmem_tiles(tq, Lay.Lg, tfirst, qi * nq_mine / 4, (qi + 1) * nq_mine / 4, T, lane, st, pv);
         tmem_wait_st();
       }
+      if ((wid & 1) != 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
       pv = warp_sum(pv);
       if (lane == 0) atomicAdd(&s_pv[s & 1], pv);
     }

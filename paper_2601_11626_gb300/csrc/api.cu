@@ -267,10 +267,6 @@ static csvd_status take_status(int* d_status, cudaStream_t s) {
 
 // Largest core kept in shared memory (bytes of dynamic shared memory).
 static constexpr int kCoreSmemBudget = 200 * 1024;
-// Eigenvalue-core launch classes: small cores share an SM; large cores get
-// all of its shared memory plus tensor memory, and the leading tile columns
-// of the largest ones a global workspace.
-static constexpr int kTriSmallN = 192;
 
 static int num_sms();
 namespace csvd {
@@ -395,7 +391,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   const int n = (int)items.size();
   if (n == 0) return CSVD_OK;
   Layout L;
-  struct Off { size_t energy, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new; bool smem; };
+  struct Off { size_t energy, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new, cls; bool smem; };
   std::vector<Off> off(n);
   const bool mixed = (precision == CSVD_MIXED) && !want_W;
   for (int i = 0; i < n; ++i) {
@@ -414,6 +410,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       o.ldwork = rt + k;
       o.smem = false;
       o.work = 0;
+      o.cls = 0;
     } else {
       o.P2 = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
       o.Rt = L.add(sizeof(float) * (size_t)k * m);
@@ -427,19 +424,18 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       o.Wt = want_W ? L.add(sizeof(float) * (size_t)std::max(o.r_new, 1) * o.nr) : 0;
     }
   }
-  // mixed form: eigen-core classes; cores too large for shared memory get a
-  // packed global workspace for their leading steps
-  int tri_nmax_small = 1, tri_nmax_large = 1;
+  // mixed form: eigen-core launch classes by core size; the leading tile
+  // columns of the largest cores get a global workspace
+  int tri_nmax[3] = {1, 1, 1};
   if (mixed) {
     for (int i = 0; i < n; ++i) {
       const int nn = items[i].st.rt + (int)items[i].blk->k;
-      if (nn <= kTriSmallN) tri_nmax_small = std::max(tri_nmax_small, nn);
-      else tri_nmax_large = std::max(tri_nmax_large, nn);
+      off[i].cls = tridiag_class(nn);
+      tri_nmax[off[i].cls] = std::max(tri_nmax[off[i].cls], nn);
     }
     for (int i = 0; i < n; ++i) {
       const int nn = items[i].st.rt + (int)items[i].blk->k;
-      off[i].smem = nn <= kTriSmallN;
-      const int64_t wf = off[i].smem ? 0 : tridiag_work_floats(nn, kTriLargeSmemBytes, tri_nmax_large);
+      const int64_t wf = tridiag_work_floats(off[i].cls, nn, tri_nmax[off[i].cls]);
       if (wf > 0) off[i].work = L.add(sizeof(float) * (size_t)wf);
     }
   }
@@ -487,7 +483,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   auto build = [&](char* base, Pack& pk, GemmBatch& gP, GemmBatch& gR, GemmBatch& gP2,
                    GemmBatch& gRu, GemmBatch& gG, std::vector<EnergyDesc>& ed,
                    std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
-                   std::vector<CoreDesc>& cd_g, std::vector<TcItem>& tci,
+                   std::vector<CoreDesc>& cd_g, std::vector<CoreDesc>& cd_m, std::vector<TcItem>& tci,
                    std::vector<TcTile>& tct) {
     pk.add(maps);
     int max_m = 1;
@@ -573,7 +569,8 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
           c.ldw = o.nr;
         }
       }
-      (o.smem ? cd_s : cd_g).push_back(c);
+      if (mixed) (o.cls == 0 ? cd_s : o.cls == 1 ? cd_m : cd_g).push_back(c);
+      else (o.smem ? cd_s : cd_g).push_back(c);
     }
     gP.pack(pk); gR.pack(pk); gP2.pack(pk); gRu.pack(pk); gG.pack(pk);
     (void)max_m;
@@ -585,12 +582,12 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   {
     Pack pk;
     GemmBatch a, b, c, d, e;
-    std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg;
+    std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg, cm;
     std::vector<TcItem> ti; std::vector<TcTile> tt;
     char* fake = reinterpret_cast<char*>(uintptr_t(1) << 20);
-    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg, ti, tt))
+    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg, cm, ti, tt))
       return fail(CSVD_ERR_UNIMPLEMENTED, "bf16 blocks need the mixed form");
-    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg); pk.add(ti); pk.add(tt);
+    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg); pk.add(cm); pk.add(ti); pk.add(tt);
     desc_bytes = pk.buf.size();
   }
   const size_t off_desc = L.add(desc_bytes);
@@ -600,10 +597,11 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   pk_base = ws.base + off_desc;
   Pack pk;
   GemmBatch gP, gR, gP2, gRu, gG;
-  std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g;
+  std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g, cd_m;
   std::vector<TcItem> tci; std::vector<TcTile> tct;
-  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g, tci, tct);
+  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g, cd_m, tci, tct);
   const size_t o_ed = pk.add(ed), o_qd = pk.add(qd), o_cs = pk.add(cd_s), o_cg = pk.add(cd_g);
+  const size_t o_cm = pk.add(cd_m);
   const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);
   char* dbase = ws.base + off_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
@@ -622,11 +620,12 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     CUDA_TRY(launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti), reinterpret_cast<TcTile*>(dbase + o_tt),
                             (int)tct.size(), num_sms(), d_status, s));
     CUDA_TRY(gG.launch(dbase, s));
-    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
-                                 kTriLargeSmemBytes, tri_nmax_large, d_status, s));
-    CUDA_TRY(launch_core_tridiag(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
-                                 tridiag_smem_bytes(tri_nmax_small, false), tri_nmax_small,
-                                 d_status, s));
+    CUDA_TRY(launch_core_tridiag(2, reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
+                                 tri_nmax[2], d_status, s));
+    CUDA_TRY(launch_core_tridiag(1, reinterpret_cast<CoreDesc*>(dbase + o_cm), (int)cd_m.size(),
+                                 tri_nmax[1], d_status, s));
+    CUDA_TRY(launch_core_tridiag(0, reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
+                                 tri_nmax[0], d_status, s));
   } else {
     CUDA_TRY(gR.launch(dbase, s));
     CUDA_TRY(gP2.launch(dbase, s));

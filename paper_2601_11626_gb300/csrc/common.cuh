@@ -154,15 +154,17 @@ cudaError_t launch_apply_q(const ApplyQDesc* d_desc, int n_items, int max_cols,
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
 int jacobi_scratch_floats(int nc);
-// Eigen core: dynamic shared memory of a launch whose largest core is n_max
-// (`large`: one CTA per SM with the maximum opt-in size and tensor memory),
-// and the global workspace (floats) a core of size n needs in that launch.
+// Eigen core launch classes by core size n (0: n <= 192, 1: n <= 320,
+// 2: larger), the dynamic shared memory of a class launch whose largest
+// core is n_max, and the global workspace (floats) a core of size n needs in
+// that launch (nonzero only for the largest cores).
 constexpr int kTriLargeSmemBytes = 227 * 1024 - 1024;
-int tridiag_smem_bytes(int n_max, bool large);
-int64_t tridiag_work_floats(int n, int smem_bytes, int n_max);
+int tridiag_class(int n);
+int tridiag_smem_bytes(int cls, int n_max);
+int64_t tridiag_work_floats(int cls, int n, int n_max);
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
                                int* d_status, cudaStream_t s);
-cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
+cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
                                 int* d_status, cudaStream_t s);
 cudaError_t launch_gram_dev(const float* U, int64_t ldu, int m, int r, float* D, cudaStream_t s);
 cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,

@@ -8,14 +8,16 @@
 // needed: sigma~_j = sqrt(lambda_j) (Cor. 3), and the tail follows from the
 // trace, sum_{j > r_new} lambda_j = tr(T) - sum_{j <= r_new} lambda_j.
 //
-// One CTA per item:
+// One CTA per item, in three launch classes by core size: 4 warps (four CTAs
+// per SM) for n <= 192, 8 warps (two per SM) for n <= 320, 16 warps (one per
+// SM) above.  Each CTA owns its SM share of tensor memory (TMEM).
 //  1. G is assembled as 32 x 32 tiles of its lower tile triangle (diagonal
 //     tiles hold both halves), listed column by column.  The tiles consumed
-//     last live in shared memory; when they do not all fit, the next ones go
-//     to tensor memory (up to 64 tiles, one tile per warp-wide 32x32b load),
-//     and only what still does not fit -- the leading tile columns of the
-//     largest cores -- stays in a global workspace.  Nothing migrates: a
-//     tile column leaves the trailing matrix before any tile could move.
+//     last -- revisited by the most steps -- live in TMEM (one tile per
+//     warp-wide 32x32b load or store); the ones before them in shared memory;
+//     only what still does not fit, the leading tile columns of the largest
+//     cores, stays in a global workspace.  Nothing migrates: a tile column
+//     leaves the trailing matrix before any tile could move.
 //  2. Householder tridiagonalisation, G <- H G H, H = I - tau v v^T, with two
 //     block barriers per step:
 //       phase A (one row per thread): w of the previous step from its p, the
@@ -27,8 +29,10 @@
 //     Vectors are indexed by global row and vanish outside the trailing
 //     range, so boundary tiles need no masks.  Column sums of off-diagonal
 //     tiles accumulate across a tile column and are reduced once per column.
-//     Global tiles are shared evenly among warps; shared-memory tiles top
-//     the warps up to equal counts around the lane-restricted TMEM tiles.
+//     A warp reaches only its TMEM lane quarter, so TMEM tiles are dealt to
+//     quarters in pairs, round-robin; shared-memory tiles top the warps up
+//     to equal counts; global tiles are shared evenly.  The shares are set
+//     once per tile column.  Tile updates use packed f32x2 FMAs.
 //  3. Multisection bisection on Sturm counts of the tridiagonal matrix for
 //     the top r_new eigenvalues (g threads per eigenvalue, the interval
 //     shrinks (g + 1)-fold per iteration).
@@ -41,55 +45,58 @@
 namespace csvd {
 namespace {
 
-constexpr int kTriThreads = 512;
-constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kBisectMax = 64;
 constexpr int kTile = 32;
 constexpr int kTileFloats = kTile * kTile;
-constexpr int kTmemTiles = 64;            // 4 lane quarters x 16 tiles of 32 columns
-constexpr int kTmemCols = 512;
-constexpr int kTmemMinSmem = 120 * 1024;  // at most one CTA per SM from this size on
-constexpr int kVecs = 9;                  // dv, ev, v (2), p (2), w, column (2)
+constexpr int kVecs = 9;  // dv, ev, v (2), p (2), w, column (2)
+constexpr int kRed = 128;
+
+struct ClassCfg {
+  int warps, max_n;
+};
+constexpr ClassCfg kClass[3] = {{4, 192}, {8, 320}, {16, 1 << 30}};
 
 __host__ __device__ __forceinline__ int tiles_in(int T) { return T * (T + 1) / 2; }
 // First list position of tile column b in a T-row lower tile triangle.
 __host__ __device__ __forceinline__ int col_start(int b, int T) { return b * T - b * (b - 1) / 2; }
 
 // Placement of the tile list of one core: positions [0, Lg) in the global
-// workspace (tile columns 0 .. g-1), [Lg, Lg + Ntm) in TMEM (tile t = L - Lg
-// at lane quarter t % 4, column 32 (t / 4)), [Ls, T(T+1)/2) in shared memory.
+// workspace (tile columns 0 .. g-1), [Lg, Lt) in shared memory (slot L - Lg),
+// [Lt, T(T+1)/2) in TMEM (tile t = L - Lt at the lane quarter and slot
+// given by tm_tile / tm_slot below, 32 columns per slot).
 struct TileLayout {
-  int T, Lg, Ntm, Ls;
+  int T, Lg, Lt, Ntm;
 };
 
 __host__ __device__ int smem_tile_cap(int smem_bytes, int n_max) {
   const int npad = (n_max + kTile - 1) / kTile * kTile;
-  const long avail = (long)smem_bytes / 4 - (long)kVecs * npad - 128;
+  const long avail = (long)smem_bytes / 4 - (long)kVecs * npad - kRed;
   return avail > 0 ? (int)(avail / kTileFloats) : 0;
 }
 
-__host__ __device__ TileLayout tile_layout(int n, int smem_bytes, int n_max) {
+__host__ __device__ TileLayout tile_layout(int n, int warps, int smem_bytes, int n_max) {
   TileLayout L;
   L.T = (n + kTile - 1) / kTile;
-  const int cs = smem_tile_cap(smem_bytes, n_max);
-  const int cap = cs + (smem_bytes >= kTmemMinSmem ? kTmemTiles : 0);
+  const int nt = tiles_in(L.T);
+  const int ct = 4 * warps;  // TMEM tiles: 32 columns per warp
+  const int cap = ct + smem_tile_cap(smem_bytes, n_max);
   int g = 0;
   while (g < L.T && tiles_in(L.T - g) > cap) ++g;
   L.Lg = col_start(g, L.T);
-  const int on = tiles_in(L.T - g);
-  L.Ntm = on > cs ? on - cs : 0;
-  L.Ls = L.Lg + L.Ntm;
+  L.Ntm = min(nt - L.Lg, ct);
+  L.Lt = nt - L.Ntm;
   return L;
 }
 
+// List position L -> tile (a, b) (rows a >= b).
 __device__ __forceinline__ void tile_of(int L, int T, int& a, int& b) {
-  b = 0;
-  int st = 0;
-  while (st + T - b <= L) {
-    st += T - b;
-    ++b;
-  }
-  a = b + (L - st);
+  const float q = (float)(2 * T + 1);
+  int bb = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)L, 0.f))) * 0.5f);
+  bb = max(0, min(bb, T - 1));
+  while (bb > 0 && col_start(bb, T) > L) --bb;
+  while (bb + 1 < T && col_start(bb + 1, T) <= L) ++bb;
+  b = bb;
+  a = bb + (L - col_start(bb, T));
 }
 
 __device__ __forceinline__ void tile_next(int& a, int& b, int T) {
@@ -130,7 +137,9 @@ struct Step {
   const float* wprev;
   float* pcur;         // p = G v accumulator
   float* cnext;        // receives column s + 1
+  float* glast;        // receives G(n-1, n-1)
   int b0, ccn, s1;     // tile column and in-tile column of s + 1; s + 1
+  int last_r;          // n - 1
   float v0;
 };
 
@@ -155,17 +164,28 @@ __device__ __forceinline__ void flush_cols(float (&cp)[32], int b, int lane, con
   for (int q = 0; q < 32; ++q) cp[q] = 0.f;
 }
 
+// Two independent single-rounding FMAs in one instruction (packed f32x2).
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1,
+                                     float c0, float c1) {
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+
 // The per-element work of a tile whose row `lane` holds val[0..31]:
-// G -= vp wp^T + wp vp^T, then row sums into rowacc and column sums into cp.
-__device__ __forceinline__ void tile_update(float (&val)[32], float (&cp)[32], float& rowacc,
-                                            float vr, int a, int b, int lane, const Step& st) {
+// G -= vp wp^T + wp vp^T, then row sums (four partial chains) and column
+// sums, two columns per instruction.
+__device__ __forceinline__ float tile_update(float (&val)[32], float (&cp)[32], float vr, int a,
+                                             int b, int lane, const Step& st) {
   const int r = a * kTile + lane;
-  const float vpr = st.vprev[r], wpr = st.wprev[r];
+  const float nvp = -st.vprev[r], nwp = -st.wprev[r];
   const float colw = (a == b) ? 0.f : vr;  // diagonal tiles: row sums cover both halves
   const float4* vc4 = reinterpret_cast<const float4*>(st.vcur + b * kTile);
   const float4* vp4 = reinterpret_cast<const float4*>(st.vprev + b * kTile);
   const float4* wp4 = reinterpret_cast<const float4*>(st.wprev + b * kTile);
   const int pq = (b == st.b0) ? st.ccn : -1;  // in-tile column holding v0
+  float ra0 = 0.f, ra1 = 0.f, ra2 = 0.f, ra3 = 0.f;
 #pragma unroll
   for (int q4 = 0; q4 < 8; ++q4) {
     float4 vc = vc4[q4];
@@ -177,18 +197,22 @@ __device__ __forceinline__ void tile_update(float (&val)[32], float (&cp)[32], f
       vc.w = u == 3 ? st.v0 : vc.w;
     }
     const float4 vp = vp4[q4], wp = wp4[q4];
-    const float vcs[4] = {vc.x, vc.y, vc.z, vc.w};
-    const float vps[4] = {vp.x, vp.y, vp.z, vp.w};
-    const float wps[4] = {wp.x, wp.y, wp.z, wp.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int cc = q4 * 4 + u;
-      const float x = fmaf(-vpr, wps[u], fmaf(-wpr, vps[u], val[cc]));
-      val[cc] = x;
-      rowacc = fmaf(x, vcs[u], rowacc);
-      cp[cc] = fmaf(x, colw, cp[cc]);
-    }
+    const int c = q4 * 4;
+    float x0, x1, x2, x3;
+    fma2(x0, x1, nwp, nwp, vp.x, vp.y, val[c], val[c + 1]);
+    fma2(x2, x3, nwp, nwp, vp.z, vp.w, val[c + 2], val[c + 3]);
+    fma2(x0, x1, nvp, nvp, wp.x, wp.y, x0, x1);
+    fma2(x2, x3, nvp, nvp, wp.z, wp.w, x2, x3);
+    val[c] = x0;
+    val[c + 1] = x1;
+    val[c + 2] = x2;
+    val[c + 3] = x3;
+    fma2(ra0, ra1, x0, x1, vc.x, vc.y, ra0, ra1);
+    fma2(ra2, ra3, x2, x3, vc.z, vc.w, ra2, ra3);
+    fma2(cp[c], cp[c + 1], x0, x1, colw, colw, cp[c], cp[c + 1]);
+    fma2(cp[c + 2], cp[c + 3], x2, x3, colw, colw, cp[c + 2], cp[c + 3]);
   }
+  return (ra0 + ra1) + (ra2 + ra3);
 }
 
 // Shared-memory tiles are row-major with 16-byte chunks XOR-swizzled by row
@@ -224,20 +248,21 @@ __device__ __forceinline__ void store_row(float* tp, int lane, const float (&val
     for (int cc = 0; cc < 32; ++cc) tp[cc * kTile + lane] = val[cc];
   }
 }
-__device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
-  return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
+
+__device__ __forceinline__ float pick(const float (&val)[32], int cc) {
+  float x = 0.f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x = (i == cc) ? val[i] : x;
+  return x;
 }
 
-// Everything after the tile's values are in val[]: column s + 1, row sums.
+// Everything after the tile's values are final: column s + 1, the last
+// diagonal element, row sums.
 __device__ __forceinline__ void tile_finish(const float (&val)[32], float rowacc, float vr, int a,
                                             int b, int lane, const Step& st, float& pv) {
   const int r = a * kTile + lane;
-  if (b == st.b0) {
-    float x = 0.f;
-#pragma unroll
-    for (int cc = 0; cc < 32; ++cc) x = (cc == st.ccn) ? val[cc] : x;
-    st.cnext[r] = x;
-  }
+  if (b == st.b0) st.cnext[r] = pick(val, st.ccn);
+  if (a == b && r == st.last_r) *st.glast = pick(val, st.last_r & 31);
   atomicAdd(&st.pcur[r], rowacc);
   pv = fmaf(rowacc, vr, pv);
 }
@@ -258,8 +283,7 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
     load_row<kRowMajor>(tp, lane, val);
     const int r = a * kTile + lane;
     const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
-    float rowacc = 0.f;
-    tile_update(val, cp, rowacc, vr, a, b, lane, st);
+    const float rowacc = tile_update(val, cp, vr, a, b, lane, st);
     store_row<kRowMajor>(tp, lane, val);
     tile_finish(val, rowacc, vr, a, b, lane, st, pv);
     const int bb = b;
@@ -268,45 +292,55 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
   }
 }
 
-// The warp's TMEM tiles: positions Lg + t, t = tfirst + 4 j, j in [ja, jb).
-__device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lg, int tfirst, int ja, int jb, int T,
+// TMEM tiles go to lane quarters in pairs: tile t sits in quarter
+// (t / 2) % 4 at slot 2 (t / 8) + t % 2.  Index j of quarter q's tiles:
+__device__ __forceinline__ int tm_tile(int q, int j) { return 8 * (j >> 1) + 2 * q + (j & 1); }
+// number of quarter-q tiles below position t
+__device__ __forceinline__ int tm_count(int q, int t) {
+  return 2 * (t >> 3) + min(max(t - 8 * (t >> 3) - 2 * q, 0), 2);
+}
+__device__ __forceinline__ uint32_t tm_slot(int t) { return (uint32_t)(((t >> 3) << 1) | (t & 1)); }
+
+// The warp's TMEM tiles: quarter q's tiles j in [ja, jb), at positions Lt + t.
+__device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, int jb, int T,
                                            int lane, const Step& st, float& pv) {
   if (ja >= jb) return;
-  int t = tfirst + 4 * ja;
+  int t = tm_tile(q, ja);
   int a, b;
-  tile_of(Lg + t, T, a, b);
+  tile_of(Lt + t, T, a, b);
   float cp[32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) cp[q] = 0.f;
-  for (int j = ja; j < jb; ++j, t += 4) {
-    const uint32_t taddr = tq + (uint32_t)(t >> 2) * 32u;
+  for (int i = 0; i < 32; ++i) cp[i] = 0.f;
+  for (int j = ja; j < jb; ++j) {
+    const uint32_t taddr = tq + tm_slot(t) * 32u;
     float val[32];
     tmem_load_tile(taddr, val);
     const int r = a * kTile + lane;
     const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
-    float rowacc = 0.f;
-    tile_update(val, cp, rowacc, vr, a, b, lane, st);
+    const float rowacc = tile_update(val, cp, vr, a, b, lane, st);
     tmem_store_tile(taddr, val);
     tile_finish(val, rowacc, vr, a, b, lane, st, pv);
     const int bb = b;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) tile_next(a, b, T);
+    const int adv = (j & 1) ? 7 : 1;  // to the quarter's next tile
+    for (int u = 0; u < adv; ++u) tile_next(a, b, T);
+    t += adv;
     if (b != bb || j + 1 == jb) flush_cols(cp, bb, lane, st, pv);
   }
 }
 
-}  // namespace
-
-__global__ void __launch_bounds__(kTriThreads)
+template <int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, 16 / kWarps)
 core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_max,
                     int* __restrict__ status) {
+  constexpr int kThreads = kWarps * 32;
+  constexpr uint32_t kTmemCols = 32u * kWarps;
   extern __shared__ __align__(16) float smem[];
   const CoreDesc d = descs[blockIdx.x];
   const int n = d.rt + d.k;
   const int npad = (n_max + kTile - 1) / kTile * kTile;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float* dv = smem;          // npad: diagonal of T
-  float* ev = dv + npad;     // npad: off-diagonal e[j] couples j, j+1
+  float* dv = smem;            // npad: diagonal of T
+  float* ev = dv + npad;       // npad: off-diagonal e[j] couples j, j+1
   float* vb0 = ev + npad;      // v of even / odd steps
   float* vb1 = ev + 2 * npad;
   float* pb0 = ev + 3 * npad;  // p of even / odd steps
@@ -314,15 +348,15 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   float* wv = ev + 5 * npad;   // w of the pending update
   float* cb0 = ev + 6 * npad;  // column s (rows >= s) / column s + 1
   float* cb1 = ev + 7 * npad;
-  float* red = ev + 8 * npad;  // 128
-  float* tsm = red + 128;      // shared-memory tiles
-  const TileLayout Lay = tile_layout(n, smem_bytes, n_max);
-  const int T = Lay.T, Nt = tiles_in(T);
+  float* red = ev + 8 * npad;  // kRed: per-warp partial sums
+  float* tsm = red + kRed;     // shared-memory tiles
+  const TileLayout Lay = tile_layout(n, kWarps, smem_bytes, n_max);
+  const int T = Lay.T;
   __shared__ uint32_t s_tmem;
-  __shared__ float s_pv[2];
+  __shared__ float s_glast;
   __shared__ double s_trace, s_energy_add;
 
-  if (n < 1 || n > n_max || Lay.Ls > Nt - 1 || Lay.Ntm > kTmemTiles ||
+  if (n < 1 || n > n_max || Lay.Lt - Lay.Lg > smem_tile_cap(smem_bytes, n_max) ||
       (Lay.Lg > 0 && d.work == nullptr)) {
     if (tid == 0) atomicOr(status, kStatusBadShape);
     return;
@@ -331,19 +365,17 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   if (use_tmem && wid == 0) tmem_alloc(&s_tmem, kTmemCols);
 
   // 1. assemble global and shared-memory tiles, the first column, zero vectors
-  for (int v = wid; v < Lay.Lg + (Nt - Lay.Ls); v += kTriWarps) {
-    const bool glob = v < Lay.Lg;
-    const int L = glob ? v : Lay.Ls + (v - Lay.Lg);
+  for (int L = wid; L < Lay.Lt; L += kWarps) {
     int a, b;
     tile_of(L, T, a, b);
     const int r = a * kTile + lane;
     float val[32];
 #pragma unroll
     for (int cc = 0; cc < 32; ++cc) val[cc] = core_gram(d, n, r, b * kTile + cc);
-    if (glob) store_row<false>(d.work + (int64_t)L * kTileFloats, lane, val);
-    else store_row<true>(tsm + (int64_t)(L - Lay.Ls) * kTileFloats, lane, val);
+    if (L < Lay.Lg) store_row<false>(d.work + (int64_t)L * kTileFloats, lane, val);
+    else store_row<true>(tsm + (int64_t)(L - Lay.Lg) * kTileFloats, lane, val);
   }
-  for (int i = tid; i < npad; i += kTriThreads) {
+  for (int i = tid; i < npad; i += kThreads) {
     vb0[i] = 0.f;
     vb1[i] = 0.f;
     pb0[i] = 0.f;
@@ -355,18 +387,15 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   // ||A||_F^2 = tr(A^T A) from the Gram's diagonal when no energy is given
   if (d.energy_add == nullptr) {
     double e = 0.0;
-    for (int i = tid; i < d.k; i += kTriThreads) e += (double)d.Gaa[(int64_t)i * d.ldb + i];
+    for (int i = tid; i < d.k; i += kThreads) e += (double)d.Gaa[(int64_t)i * d.ldb + i];
     e = warp_sum_d(e);
     if (lane == 0) reinterpret_cast<double*>(red)[wid] = e;
   }
-  if (tid == 0) {
-    s_pv[0] = 0.f;
-    s_pv[1] = 0.f;
-  }
+  if (tid == 0) s_glast = core_gram(d, n, n - 1, n - 1);
   __syncthreads();
   if (tid == 0 && d.energy_add == nullptr) {
     double t = 0.0;
-    for (int w = 0; w < kTriWarps; ++w) t += reinterpret_cast<double*>(red)[w];
+    for (int w = 0; w < kWarps; ++w) t += reinterpret_cast<double*>(red)[w];
     s_energy_add = t;
   }
   uint32_t tq = 0;  // TMEM address of this warp's lane quarter
@@ -374,26 +403,28 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     tmem_fence_after();
     const int q = wid & 3;
     tq = s_tmem + ((uint32_t)(q * 32) << 16);
-    for (int t = q + 4 * (wid >> 2); t < Lay.Ntm; t += 16) {
+    for (int j = wid >> 2;; j += kWarps / 4) {
+      const int t = tm_tile(q, j);
+      if (t >= Lay.Ntm) break;
       int a, b;
-      tile_of(Lay.Lg + t, T, a, b);
+      tile_of(Lay.Lt + t, T, a, b);
       const int r = a * kTile + lane;
       float val[32];
 #pragma unroll
       for (int cc = 0; cc < 32; ++cc) val[cc] = core_gram(d, n, r, b * kTile + cc);
-      tmem_store_tile(tq + (uint32_t)(t >> 2) * 32u, val);
+      tmem_store_tile(tq + tm_slot(t) * 32u, val);
     }
     tmem_wait_st();
     tmem_fence_before();
   }
   __syncthreads();
+  float* pvred = red + 64;  // per-warp p^T v partials of the last main pass
+  if (tid < kWarps) pvred[tid] = 0.f;
+  __syncthreads();
 
-  // 2. tridiagonalisation.  Per step s, two block barriers:
-  //   A (all threads, one row each): w of the previous step, the pending
-  //     update on column s, v_s below s + 1, zeroed p_s, partial ||x||^2;
-  //   B (every thread, redundantly): the reflector scalars; then the main
-  //     pass over the trailing tiles.
+  // 2. tridiagonalisation (see the file comment for the two phases)
   float tau_prev = 0.f;  // tau of the pending reflector (same in every thread)
+  int as_glo = 0, as_ghi = 0, as_slo = 0, as_shi = 0, as_ja = 0, as_jb = 0;  // the warp's share
   for (int s = 0;; ++s) {
     const bool odd = (s & 1) != 0;
     float* vcur = odd ? vb1 : vb0;
@@ -405,12 +436,15 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     const bool last = s + 2 >= n;
     const int b0 = (s + 1) >> 5;
     {
-      const float kk = (s >= 1) ? 0.5f * tau_prev * tau_prev * s_pv[(s + 1) & 1] : 0.f;
+      float pvs = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) pvs += pvred[w];
+      const float kk = (s >= 1) ? 0.5f * tau_prev * tau_prev * pvs : 0.f;
       const float vs = vprev[s];
       const float ws = (s >= 1) ? fmaf(tau_prev, pprev[s], -kk * vs) : 0.f;
       const int ilo = min(s, b0 * kTile);  // rows the main pass of this step touches start here
       float part = 0.f;
-      for (int i = ilo + tid; i < npad; i += kTriThreads) {
+      for (int i = ilo + tid; i < npad; i += kThreads) {
         const float vp = vprev[i];
         float w = 0.f;
         if (s >= 1 && i >= s) w = fmaf(tau_prev, pprev[i], -kk * vp);
@@ -426,20 +460,18 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       }
       part = warp_sum(part);
       if (lane == 0) red[wid] = part;
-      if (tid == 0) s_pv[s & 1] = 0.f;
     }
     __syncthreads();
     float tail2 = 0.f;
-    for (int w = 0; w < kTriWarps; ++w) tail2 += red[w];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tail2 += red[w];
     if (last) {
       if (tid == 0) {
         if (n >= 2) {
           const int j = n - 1;
-          const float* tl = tsm + (int64_t)(Nt - 1 - Lay.Ls) * kTileFloats;
-          const float gjj = smem_tile_elem(tl, j & 31, j & 31);
           dv[j - 1] = ccur[j - 1];
           ev[j - 1] = ccur[j];
-          dv[j] = fmaf(-2.f * vprev[j], wv[j], gjj);
+          dv[j] = fmaf(-2.f * vprev[j], wv[j], s_glast);
         } else {
           dv[0] = ccur[0];
         }
@@ -464,49 +496,65 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     tau_prev = tau;
     if (use_tmem) tmem_fence_after();
 
-    // main pass over the trailing tiles (tile columns >= b0)
-    {
-      const Step st{vcur, vprev, wv, pcur, cnext, b0, (s + 1) & 31, s + 1, v0};
+    // main pass over the trailing tiles (tile columns >= b0); the warp's
+    // share changes only when b0 does
+    if (s == 0 || ((s + 1) & 31) == 0) {
       const int L0 = col_start(b0, T);
       const int ng = max(0, Lay.Lg - L0);  // trailing tiles in global memory
-      const int Ls0 = max(L0, Lay.Ls);
-      const int ns = Nt - Ls0;             // ... in shared memory
-      const int t0 = max(0, L0 - Lay.Lg);  // first trailing TMEM tile
-      // TMEM tiles: quarter u & 3, split in four among its warps
-      int cu = 0, nq_mine = 0;
-      if (use_tmem) {
-        const int qq = lane & 3, f = t0 + ((qq - t0) & 3);
-        const int nq = Lay.Ntm > f ? (Lay.Ntm - f + 3) >> 2 : 0;  // lane: its quarter's count
-        const int ui = (lane >> 2) & 3;
-        cu = (lane < kTriWarps) ? (ui + 1) * nq / 4 - ui * nq / 4 : 0;
-        nq_mine = __shfl_sync(0xffffffffu, nq, wid & 3);
+      const int Ls0 = max(L0, Lay.Lg);
+      const int ns = max(0, Lay.Lt - Ls0);  // ... in shared memory
+      const int t0 = max(L0, Lay.Lt) - Lay.Lt;  // first trailing TMEM tile
+      // TMEM tiles of quarter q, split evenly among its warps
+      constexpr int kPerQ = kWarps / 4;
+      const int q = wid & 3, qi = wid >> 2;
+      const int j0 = tm_count(q, t0), nq = tm_count(q, Lay.Ntm) - j0;
+      as_ja = j0 + qi * nq / kPerQ;
+      as_jb = j0 + (qi + 1) * nq / kPerQ;
+      int s_lo, s_hi;
+      if (Lay.Ntm - t0 <= 0) {
+        s_lo = ns * wid / kWarps;
+        s_hi = ns * (wid + 1) / kWarps;
+      } else {
+        // shared-memory tiles top every warp up to the same level
+        int cu = 0;
+        if (lane < kWarps) {
+          const int lq = lane & 3, lqi = lane >> 2;
+          const int lj0 = tm_count(lq, t0), ln = tm_count(lq, Lay.Ntm) - lj0;
+          cu = (lqi + 1) * ln / kPerQ - lqi * ln / kPerQ;
+        }
+        const int ntm = Lay.Ntm - t0;
+        int lam = (ns + ntm + kWarps - 1) / kWarps;
+        for (;;) {
+          const int dd = (lane < kWarps) ? max(0, lam - cu) : 0;
+          if ((int)__reduce_add_sync(0xffffffffu, (unsigned)dd) >= ns) break;
+          ++lam;
+        }
+        const int dmine = (lane < kWarps) ? max(0, lam - cu) : 0;
+        const int before =
+            (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < wid ? dmine : 0));
+        const int mine = __shfl_sync(0xffffffffu, dmine, wid);
+        s_lo = min(before, ns);
+        s_hi = min(ns, before + mine);
       }
-      const int ntm = __reduce_add_sync(0xffffffffu, (unsigned)cu);
-      // shared-memory tiles top every warp up to the same level (water-filling)
-      int lam = (ns + ntm + kTriWarps - 1) / kTriWarps;
-      for (;;) {
-        const int dd = (lane < kTriWarps) ? max(0, lam - cu) : 0;
-        if ((int)__reduce_add_sync(0xffffffffu, (unsigned)dd) >= ns) break;
-        ++lam;
-      }
-      const int dmine = (lane < kTriWarps) ? max(0, lam - cu) : 0;
-      const int before = (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < wid ? dmine : 0));
-      const int mine = __shfl_sync(0xffffffffu, dmine, wid);
-      const int s_lo = min(before, ns), s_hi = min(ns, before + mine);
+      as_slo = Ls0 + s_lo;
+      as_shi = Ls0 + s_hi;
       // global tiles: an even share each; half the warps take them first
-      const int g_lo = L0 + ng * wid / kTriWarps, g_hi = L0 + ng * (wid + 1) / kTriWarps;
+      as_glo = L0 + ng * wid / kWarps;
+      as_ghi = L0 + ng * (wid + 1) / kWarps;
+    }
+    {
+      const Step st{vcur, vprev, wv, pcur, cnext, &s_glast, b0, (s + 1) & 31, s + 1, n - 1, v0};
+      const int g_lo = as_glo, g_hi = as_ghi;
       float pv = 0.f;
       if ((wid & 1) == 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
-      mem_tiles<true>(tsm, Lay.Ls, Ls0 + s_lo, Ls0 + s_hi, T, lane, st, pv);
+      mem_tiles<true>(tsm, Lay.Lg, as_slo, as_shi, T, lane, st, pv);
       if (use_tmem) {
-        const int q = wid & 3, qi = wid >> 2;
-        const int tfirst = t0 + ((q - t0) & 3);
-        tmem_tiles(tq, Lay.Lg, tfirst, qi * nq_mine / 4, (qi + 1) * nq_mine / 4, T, lane, st, pv);
+        tmem_tiles(tq, Lay.Lt, wid & 3, as_ja, as_jb, T, lane, st, pv);
         tmem_wait_st();
       }
       if ((wid & 1) != 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
       pv = warp_sum(pv);
-      if (lane == 0) atomicAdd(&s_pv[s & 1], pv);
+      if (lane == 0) pvred[wid] = pv;
     }
     if (use_tmem) tmem_fence_before();
     __syncthreads();
@@ -520,7 +568,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   // 3. Gershgorin interval, trace, squared off-diagonals
   float lo = 3.0e38f, hi = -3.0e38f, emax = 0.f;
   double tr = 0.0;
-  for (int i = tid; i < n; i += kTriThreads) {
+  for (int i = tid; i < n; i += kThreads) {
     const float el = i > 0 ? fabsf(ev[i - 1]) : 0.f;
     const float er = i + 1 < n ? fabsf(ev[i]) : 0.f;
     lo = fminf(lo, dv[i] - el - er);
@@ -528,8 +576,8 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     emax = fmaxf(emax, er * er);
     tr += (double)dv[i];
   }
-  __shared__ float s_lo[kTriWarps], s_hi[kTriWarps], s_em[kTriWarps];
-  __shared__ double s_tr[kTriWarps];
+  __shared__ float s_lo[kWarps], s_hi[kWarps], s_em[kWarps];
+  __shared__ double s_tr[kWarps];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -541,7 +589,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   __syncthreads();
   float glo = s_lo[0], ghi = s_hi[0], gem = s_em[0];
   double gtr = s_tr[0];
-  for (int w = 1; w < kTriWarps; ++w) {
+  for (int w = 1; w < kWarps; ++w) {
     glo = fminf(glo, s_lo[w]);
     ghi = fmaxf(ghi, s_hi[w]);
     gem = fmaxf(gem, s_em[w]);
@@ -549,7 +597,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   }
   float* e2 = vb0;  // reuse
   float* lam = pb0;
-  for (int i = tid; i < n; i += kTriThreads) e2[i] = (i + 1 < n) ? ev[i] * ev[i] : 0.f;
+  for (int i = tid; i < n; i += kThreads) e2[i] = (i + 1 < n) ? ev[i] * ev[i] : 0.f;
   if (tid == 0) s_trace = gtr;
   __syncthreads();
 
@@ -559,8 +607,8 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   const float atol = 2.4e-7f * gnorm + 1e-30f;
   const int rq = d.r_new;
   int g = 1;
-  while (g < 16 && g * 2 * rq <= kTriThreads) g *= 2;
-  const int ngroups = kTriThreads / g;
+  while (g < 16 && g * 2 * rq <= kThreads) g *= 2;
+  const int ngroups = kThreads / g;
   const int grp = tid / g, sub = tid % g;
   int capped = 0;
   for (int q0 = 0; q0 < rq; q0 += ngroups) {  // uniform trip count across the block
@@ -619,30 +667,53 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   }
 }
 
-int tridiag_smem_bytes(int n_max, bool large) {
-  if (large) return kTriLargeSmemBytes;
+}  // namespace
+
+int tridiag_class(int n) {
+  for (int c = 0; c < 2; ++c)
+    if (n <= kClass[c].max_n) return c;
+  return 2;
+}
+
+int tridiag_smem_bytes(int cls, int n_max) {
+  if (cls == 2) return kTriLargeSmemBytes;
+  // at most the class's SM share of shared memory, less when the cores are small
+  const int share = (cls == 0) ? 56 * 1024 : 112 * 1024;
   const int npad = (n_max + kTile - 1) / kTile * kTile;
   const int T = npad / kTile;
-  return (kVecs * npad + 128 + tiles_in(T) * kTileFloats) * 4;
+  const int need_tiles = max(0, tiles_in(T) - 4 * kClass[cls].warps);
+  const int need = (kVecs * npad + kRed + need_tiles * kTileFloats) * 4;
+  return min(need, share);
 }
 
-int64_t tridiag_work_floats(int n, int smem_bytes, int n_max) {
-  return (int64_t)tile_layout(n, smem_bytes, n_max).Lg * kTileFloats;
+int64_t tridiag_work_floats(int cls, int n, int n_max) {
+  return (int64_t)tile_layout(n, kClass[cls].warps, tridiag_smem_bytes(cls, n_max), n_max).Lg *
+         kTileFloats;
 }
 
-cudaError_t launch_core_tridiag(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
+template <int kWarps>
+static cudaError_t launch_class(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
                                 int* d_status, cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
   if (smem_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel,
+    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel<kWarps>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
   }
   prof_begin(s);
-  core_tridiag_kernel<<<n_items, kTriThreads, smem_bytes, s>>>(d_desc, smem_bytes, n_max,
-                                                               d_status);
-  prof_end("core_tridiag", s);
+  core_tridiag_kernel<kWarps><<<n_items, kWarps * 32, smem_bytes, s>>>(d_desc, smem_bytes, n_max,
+                                                                        d_status);
+  prof_end(kWarps == 4 ? "core_tridiag.small" : kWarps == 8 ? "core_tridiag.medium"
+                                                            : "core_tridiag.large", s);
   return cudaGetLastError();
+}
+
+cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
+                                int* d_status, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const int smem = tridiag_smem_bytes(cls, n_max);
+  if (cls == 0) return launch_class<4>(d_desc, n_items, smem, n_max, d_status, s);
+  if (cls == 1) return launch_class<8>(d_desc, n_items, smem, n_max, d_status, s);
+  return launch_class<16>(d_desc, n_items, smem, n_max, d_status, s);
 }
 
 }  // namespace csvd

@@ -25,7 +25,6 @@ constexpr size_t kScratchBytes = size_t(4) << 20;  // 4 MiB per GPU
 constexpr int kMaxK = 512;
 constexpr int kMaxRt = 128;
 constexpr int kMaxTiles = 4 + 10;  // P tiles (rt <= 128, k <= 512) + upper G tiles
-constexpr int kSmallN = 192;
 
 struct Descs {
   CoreDesc core;
@@ -71,9 +70,8 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   if (rt > 0 && (st->r & 3) != 0)
     return set_error(CSVD_ERR_SHAPE, "needs a state rank cap r divisible by 4");
   const int n = rt + k;
-  const bool small = n <= kSmallN;
-  const int smem = small ? tridiag_smem_bytes(n, false) : kTriLargeSmemBytes;
-  const int64_t work_floats = small ? 0 : tridiag_work_floats(n, smem, n);
+  const int cls = tridiag_class(n);
+  const int64_t work_floats = tridiag_work_floats(cls, n, n);
   if ((size_t)kOffWork + (size_t)work_floats * 4 > kScratchBytes)
     return set_error(CSVD_ERR_SHAPE, "scratch limit exceeded");
 
@@ -141,7 +139,7 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   if (e == cudaSuccess) e = launch_energy(&ddesc->energy, 1, chunks, s);
   if (e == cudaSuccess)
     e = launch_tc_gram(&ddesc->item, ddesc->tiles, nt, device_sm_count(), st->status, s);
-  if (e == cudaSuccess) e = launch_core_tridiag(&ddesc->core, 1, smem, n, st->status, s);
+  if (e == cudaSuccess) e = launch_core_tridiag(cls, &ddesc->core, 1, n, st->status, s);
   if (e != cudaSuccess)
     return set_error(CSVD_ERR_CUDA, cudaGetErrorString(e));
   return CSVD_OK;

@@ -404,9 +404,11 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     o.nc = rt + k;
     o.r_new = std::min(it.r, o.nr);
     o.energy = L.add(sizeof(double));
-    o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * k) : 0;
+    // mixed form: P and A^T A rows padded to 4 floats (16-byte stores)
+    const int kld = mixed ? (k + 3) & ~3 : k;
+    o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * kld) : 0;
     if (mixed) {
-      o.G = L.add(sizeof(float) * (size_t)k * k);
+      o.G = L.add(sizeof(float) * (size_t)k * kld);
       o.ldwork = rt + k;
       o.smem = false;
       o.work = 0;
@@ -498,14 +500,15 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
       float* P = rt > 0 ? reinterpret_cast<float*>(base + o.P) : nullptr;
       EnergyDesc e{it.blk->ptr, it.blk->ld, (int)m, k, bf, 0, energy};
       ed.push_back(e);
+      const int kld = mixed ? (k + 3) & ~3 : k;
       if (rt > 0 && !tc_ok[i])
-        gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, k, 0, rt, k, (int)m,
+        gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, kld, 0, rt, k, (int)m,
                     1.f, nullptr, 0, 0, 0.f, 0, bf));
       CoreDesc c;
       std::memset(&c, 0, sizeof(c));
       c.P = P;
       c.P2 = nullptr;
-      c.ldp = k;
+      c.ldp = kld;
       c.sigma = it.st.sigma;
       c.scal = it.st.scal;
       // mixed form: the eigen core takes ||A||^2 from the trace of A^T A
@@ -528,7 +531,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
         if (tc_ok[i]) {
           const int id = (int)tci.size();
           TcItem ti{reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, it.st.U,
-                    it.st.ldu, (int)m, k, rt, 0, P, k, G, k, nullptr, nullptr};
+                    it.st.ldu, (int)m, k, rt, 0, P, kld, G, kld, nullptr, nullptr};
           if (mapA_idx[i] >= 0 && (rt == 0 || mapU_idx[i] >= 0)) {
             // maps are the first array of the descriptor region
             ti.mapA = pk_base + (size_t)mapA_idx[i] * sizeof(CUtensorMap);
@@ -540,11 +543,11 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
           for (int r0 = 0; r0 < k; r0 += kTcBM)
             for (int c0 = r0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 1, r0, c0});
         } else {
-          gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, k, 0, k, k,
+          gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, kld, 0, k, k,
                       (int)m, 1.f, nullptr, 0, 0, 0.f, bf, bf), true);
         }
         c.Gaa = G;
-        c.ldb = k;
+        c.ldb = kld;
         c.work = o.work ? reinterpret_cast<float*>(base + o.work) : nullptr;
       } else {
         if (bf) return false;

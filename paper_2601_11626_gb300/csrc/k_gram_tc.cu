@@ -14,10 +14,12 @@
 // Structure: persistent CTAs walk a list of 128 x 128 output tiles (tiles of
 // one candidate are adjacent so its columns stay in L2 while they are
 // reused).  Warp roles, connected by mbarrier rings:
-//   warp 0      bulk (TMA) copies of 32 f32 rows of each operand into a
-//               staging buffer (one cp.async.bulk per row and lane)
-//   warps 2-9   split staging f32 -> bf16 hi/lo, written K-major with the
-//               64-byte swizzle the UMMA descriptors expect
+//   warp 0      TMA: one 2-D tensor box (32 rows x 128 f32 columns, zero
+//               outside the matrix) per operand into a 5-deep staging ring
+//               (one cp.async.bulk per row when no tensor map is given)
+//   warps 2-9   split staging f32 -> bf16 hi/lo into a 2-deep operand
+//               ring, K-major with the 64-byte swizzle the UMMA
+//               descriptors expect
 //   warp 1      one thread issues tcgen05.mma (M = N = 128, K = 16) into a
 //               double-buffered f32 accumulator in TMEM and commits
 //   warps 10-13 tcgen05.ld the finished accumulator and store it
@@ -29,13 +31,17 @@
 namespace csvd {
 namespace {
 
-constexpr int kStA = 0;                          // f32 [32][128]
-constexpr int kStB = kStA + kTcBK * kTcBM * 4;   // f32 [32][128]
-constexpr int kAhi = kStB + kTcBK * kTcBN * 4;   // bf16 [128][32] swizzled
+// staging slot: f32 [32][128] for each operand
+constexpr int kStA = 0;
+constexpr int kStB = kStA + kTcBK * kTcBM * 4;
+static_assert(kStB + kTcBK * kTcBN * 4 == kTcStageF, "staging layout");
+// operand slot: bf16 [128][32] swizzled, hi and lo of each operand
+constexpr int kAhi = 0;
 constexpr int kAlo = kAhi + kTcBM * kTcBK * 2;
 constexpr int kBhi = kAlo + kTcBM * kTcBK * 2;
 constexpr int kBlo = kBhi + kTcBN * kTcBK * 2;
-static_assert(kBlo + kTcBN * kTcBK * 2 == kTcStageBytes, "stage layout");
+static_assert(kBlo + kTcBN * kTcBK * 2 == kTcStageB, "operand layout");
+constexpr int kOpBase = kTcStagesF * kTcStageF;  // operand ring after the staging ring
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, both
@@ -185,23 +191,21 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return lo | (hi << 16);
 }
 
-// Split 8 f32 values of one row/chunk into hi and lo bf16 chunks.
+// Split 8 f32 values of one row/chunk into hi and lo bf16 chunks
+// (x = hi + lo + a remainder below 2^-17 |x|), two values per conversion.
 __device__ __forceinline__ void split_store(uint8_t* hi_base, uint8_t* lo_base, uint32_t off,
                                             const float* x) {
-  float h[8], l[8];
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const __nv_bfloat16 hb = __float2bfloat16_rn(x[e]);
-    h[e] = __bfloat162float(hb);
-    l[e] = x[e] - h[e];
+  for (int p = 0; p < 4; ++p) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
+    h[p] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[p] = *reinterpret_cast<const uint32_t*>(&lb);
   }
-  uint4 vh, vl;
-  vh.x = pack_bf16(h[0], h[1]); vh.y = pack_bf16(h[2], h[3]);
-  vh.z = pack_bf16(h[4], h[5]); vh.w = pack_bf16(h[6], h[7]);
-  vl.x = pack_bf16(l[0], l[1]); vl.y = pack_bf16(l[2], l[3]);
-  vl.z = pack_bf16(l[4], l[5]); vl.w = pack_bf16(l[6], l[7]);
-  *reinterpret_cast<uint4*>(hi_base + off) = vh;
-  *reinterpret_cast<uint4*>(lo_base + off) = vl;
+  *reinterpret_cast<uint4*>(hi_base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_base + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 struct TileInfo {
@@ -254,24 +258,27 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcStages * kTcStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOpBase + kTcStagesB * kTcStageB);
   // barrier slots
   const uint32_t b0 = smem_u32(bars);
+  constexpr int F = kTcStagesF, B = kTcStagesB;
   auto full_st = [&](int s) { return b0 + 8u * s; };
-  auto empty_st = [&](int s) { return b0 + 8u * (kTcStages + s); };
-  auto full_bf = [&](int s) { return b0 + 8u * (2 * kTcStages + s); };
-  auto empty_bf = [&](int s) { return b0 + 8u * (3 * kTcStages + s); };
-  auto tmem_full = [&](int a) { return b0 + 8u * (4 * kTcStages + a); };
-  auto tmem_empty = [&](int a) { return b0 + 8u * (4 * kTcStages + 2 + a); };
-  const uint32_t final_bar = b0 + 8u * (4 * kTcStages + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4 * kTcStages + 5);
+  auto empty_st = [&](int s) { return b0 + 8u * (F + s); };
+  auto full_bf = [&](int s) { return b0 + 8u * (2 * F + s); };
+  auto empty_bf = [&](int s) { return b0 + 8u * (2 * F + B + s); };
+  auto tmem_full = [&](int a) { return b0 + 8u * (2 * F + 2 * B + a); };
+  auto tmem_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + 2 + a); };
+  const uint32_t final_bar = b0 + 8u * (2 * F + 2 * B + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F + 2 * B + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < kTcStagesF; ++s) {
       mbar_init(full_st(s), 1);
       mbar_init(empty_st(s), 8);
+    }
+    for (int s = 0; s < kTcStagesB; ++s) {
       mbar_init(full_bf(s), 8);
       mbar_init(empty_bf(s), 1);
     }
@@ -305,13 +312,13 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
       const bool use_map = ti.mapa != nullptr && ti.mapb != nullptr;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int slot = it % kTcStages;
-        const uint32_t ph = (it / kTcStages) & 1u;
+        const int slot = it % kTcStagesF;
+        const uint32_t ph = (it / kTcStagesF) & 1u;
         if (!warp_wait(empty_st(slot), ph ^ 1u, abort_flag)) { ok = false; break; }
         if (use_map) {
           // one tensor box per operand: full box bytes (zero-filled outside)
           if (lane == 0) {
-            uint8_t* st = smem + slot * kTcStageBytes;
+            uint8_t* st = smem + slot * kTcStageF;
             const uint32_t box = (uint32_t)(kTcBK * kTcBM * 4);
             mbar_arrive_tx(full_st(slot), ti.diag ? box : 2u * box);
             tma_box(smem_u32(st + kStA), ti.mapa, ti.xa, kb * kTcBK, full_st(slot));
@@ -325,7 +332,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         __syncwarp();
         if (lane < rows) {
           const int64_t l = (int64_t)kb * kTcBK + lane;
-          uint8_t* st = smem + slot * kTcStageBytes;
+          uint8_t* st = smem + slot * kTcStageF;
           bulk_g2s(smem_u32(st + kStA + lane * (kTcBM * 4)), ti.Xa + l * ti.lda, bytesA,
                    full_st(slot));
           if (!ti.diag)
@@ -336,9 +343,9 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     }
     // drain copies still in flight (all consumed on a normal exit)
     if (lane == 0) {
-      const uint32_t n_last = it < (uint32_t)kTcStages ? it : (uint32_t)kTcStages;
+      const uint32_t n_last = it < (uint32_t)kTcStagesF ? it : (uint32_t)kTcStagesF;
       for (uint32_t j = it - n_last; j < it; ++j)
-        mbar_wait(full_st(j % kTcStages), (j / kTcStages) & 1u, abort_flag, false);
+        mbar_wait(full_st(j % kTcStagesF), (j / kTcStagesF) & 1u, abort_flag, false);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -354,11 +361,11 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         tc_fence_after();
         const uint32_t dt = tmem_base + acc * (uint32_t)kTcBN;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int slot = it % kTcStages;
-          const uint32_t ph = (it / kTcStages) & 1u;
+          const int slot = it % kTcStagesB;
+          const uint32_t ph = (it / kTcStagesB) & 1u;
           if (!mbar_wait(full_bf(slot), ph, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          uint8_t* st = smem + slot * kTcStageBytes;
+          uint8_t* st = smem + kOpBase + slot * kTcStageB;
           const uint32_t ahi = smem_u32(st + kAhi), alo = smem_u32(st + kAlo);
           const uint32_t bhi = ti.diag ? ahi : smem_u32(st + kBhi);
           const uint32_t blo = ti.diag ? alo : smem_u32(st + kBlo);
@@ -391,40 +398,60 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
       const TileInfo ti = tile_info(items, tiles[tt]);
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
+      const bool masked = ti.mapa == nullptr || ti.mapb == nullptr;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int slot = it % kTcStages;
-        const uint32_t ph = (it / kTcStages) & 1u;
-        if (!warp_wait(full_st(slot), ph, abort_flag)) { ok = false; break; }
-        if (!warp_wait(empty_bf(slot), ph ^ 1u, abort_flag)) { ok = false; break; }
-        uint8_t* st = smem + slot * kTcStageBytes;
+        const int fs = it % kTcStagesF, bs = it % kTcStagesB;
+        if (!warp_wait(full_st(fs), (it / kTcStagesF) & 1u, abort_flag)) { ok = false; break; }
+        if (!warp_wait(empty_bf(bs), ((it / kTcStagesB) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        const uint8_t* st = smem + fs * kTcStageF;
+        uint8_t* op = smem + kOpBase + bs * kTcStageB;
         const float* sa = reinterpret_cast<const float*>(st + kStA);
         const float* sb = reinterpret_cast<const float*>(st + kStB);
-        const int lmax = ti.m - kb * kTcBK;
+        if (masked) {
+          // per-row copies leave rows past m and columns past k unwritten
+          const int lmax = ti.m - kb * kTcBK;
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = c0 + cc;
-          const uint32_t off = sw64_off(row, c);
-          float x[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int l = c * 8 + e;
-            x[e] = (l < lmax && row < ti.validA) ? sa[l * kTcBM + row] : 0.f;
-          }
-          split_store(st + kAhi, st + kAlo, off, x);
-          if (!ti.diag) {
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = c0 + cc;
+            const uint32_t off = sw64_off(row, c);
+            float x[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int l = c * 8 + e;
-              x[e] = (l < lmax && row < ti.validB) ? sb[l * kTcBN + row] : 0.f;
+              x[e] = (l < lmax && row < ti.validA) ? sa[l * kTcBM + row] : 0.f;
             }
-            split_store(st + kBhi, st + kBlo, off, x);
+            split_store(op + kAhi, op + kAlo, off, x);
+            if (!ti.diag) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int l = c * 8 + e;
+                x[e] = (l < lmax && row < ti.validB) ? sb[l * kTcBN + row] : 0.f;
+              }
+              split_store(op + kBhi, op + kBlo, off, x);
+            }
+          }
+        } else {
+          // tensor boxes arrive zero-filled outside the matrix
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = c0 + cc;
+            const uint32_t off = sw64_off(row, c);
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = sa[(c * 8 + e) * kTcBM + row];
+            split_store(op + kAhi, op + kAlo, off, x);
+            if (!ti.diag) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) x[e] = sb[(c * 8 + e) * kTcBN + row];
+              split_store(op + kBhi, op + kBlo, off, x);
+            }
           }
         }
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(full_bf(slot));
-          mbar_arrive(empty_st(slot));
+          mbar_arrive(full_bf(bs));
+          mbar_arrive(empty_st(fs));
         }
       }
     }
@@ -438,15 +465,32 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       if (!warp_wait(tmem_full(acc), aph, abort_flag)) break;
       tc_fence_after();
       const int r = q * 32 + lane;
+      const bool vec = (ti.ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(ti.out) & 15) == 0;
 #pragma unroll 1
       for (int cc = 0; cc < kTcBN / 32; ++cc) {
+        const int nv = ti.validB - cc * 32;  // valid columns of this chunk (same in every lane)
+        if (nv <= 0) break;
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)kTcBN + cc * 32, v);
         if (r < ti.validA) {
           float* o = ti.out + (int64_t)r * ti.ldo + cc * 32;
+          if (vec) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (cc * 32 + e < ti.validB) o[e] = v[e];
+            for (int e4 = 0; e4 < 8; ++e4) {
+              const int e = 4 * e4;
+              if (e + 3 < nv) {
+                *reinterpret_cast<float4*>(o + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+              } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (e + u < nv) o[e + u] = v[e + u];
+              }
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+              if (e < nv) o[e] = v[e];
+          }
         }
       }
       tc_fence_before();

@@ -102,8 +102,9 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   Descs h;
   std::memset(&h, 0, sizeof(h));
   h.energy = EnergyDesc{A->ptr, A->ld, (int)m, k, 0, 0, energy};
+  const int kld = (k + 3) & ~3;  // 16-byte rows for the Gram kernel's stores
   h.item = TcItem{reinterpret_cast<const float*>(A->ptr), A->ld, st->U[st->cur], st->r, (int)m, k,
-                  rt, 0, P, k, G, k};
+                  rt, 0, P, kld, G, kld};
   int nt = 0;
   for (int r0 = 0; r0 < rt; r0 += kTcBM)
     for (int c0 = 0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 0, r0, c0};
@@ -111,9 +112,9 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
     for (int c0 = r0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 1, r0, c0};
   CoreDesc& c = h.core;
   c.P = rt > 0 ? P : nullptr;
-  c.ldp = k;
+  c.ldp = kld;
   c.Gaa = G;
-  c.ldb = k;
+  c.ldb = kld;
   c.sigma = st->sigma;
   c.scal = st->scal;
   c.energy_add = energy;

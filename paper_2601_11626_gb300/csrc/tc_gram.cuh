@@ -16,7 +16,7 @@ struct TcItem {
   float* P;      // rt x k, row-major ldp:  P = U^T A
   int64_t ldp;
   float* G;      // k x k, row-major ldg:   G = A^T A (tiles on and above the diagonal)
-  int64_t ldg;
+  int64_t ldg;   // P and G take 16-byte stores when ldp, ldg % 4 == 0 and 16-byte aligned
   const void* mapA;  // optional 2-D TMA tensor map of A (box 32 rows x 128 cols), device memory
   const void* mapU;  // optional tensor map of U (same box); both or neither
 };
@@ -26,10 +26,14 @@ struct TcTile {
   int item, kind, row0, col0;
 };
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcStages = 3;
+// Two rings: f32 staging slots filled by TMA (deep, to cover the load
+// latency) and split bf16 operand slots read by the MMAs.
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32;
+constexpr int kTcStagesF = 5, kTcStagesB = 2;
 constexpr int kTcThreads = 14 * 32;
-constexpr int kTcStageBytes = 2 * kTcBK * kTcBM * 4 + 4 * kTcBM * kTcBK * 2;  // 64 KB
-constexpr int kTcSmemBytes = kTcStages * kTcStageBytes + 2048;
+constexpr int kTcStageF = 2 * kTcBK * kTcBM * 4;  // 32 KB: A and B rows, f32
+constexpr int kTcStageB = 4 * kTcBM * kTcBK * 2;  // 32 KB: A hi/lo, B hi/lo, bf16
+constexpr int kTcSmemBytes = kTcStagesF * kTcStageF + kTcStagesB * kTcStageB + 2048;
 
 cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles,
                            int n_ctas, int* d_status, cudaStream_t s);

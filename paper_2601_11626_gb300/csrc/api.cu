@@ -394,6 +394,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   struct Off { size_t energy, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new, cls; bool smem; };
   std::vector<Off> off(n);
   const bool mixed = (precision == CSVD_MIXED) && !want_W;
+  const size_t energies = L.add(sizeof(double) * (size_t)n);  // one array, zeroed at once
   for (int i = 0; i < n; ++i) {
     const Item& it = items[i];
     const int64_t m = it.m;
@@ -403,7 +404,7 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
     o.nr = rt + o.kp;
     o.nc = rt + k;
     o.r_new = std::min(it.r, o.nr);
-    o.energy = L.add(sizeof(double));
+    o.energy = energies + sizeof(double) * (size_t)i;
     // mixed form: P and A^T A rows padded to 4 floats (16-byte stores)
     const int kld = mixed ? (k + 3) & ~3 : k;
     o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * kld) : 0;
@@ -608,8 +609,8 @@ static csvd_status run_items(const std::vector<Item>& items, double eps, int pre
   const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);
   char* dbase = ws.base + off_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
-  // energies start at zero
-  for (int i = 0; i < n; ++i) CUDA_TRY(cudaMemsetAsync(ws.base + off[i].energy, 0, 8, s));
+  // block energies start at zero (the mixed form takes them from tr(A^T A))
+  if (!mixed) CUDA_TRY(cudaMemsetAsync(ws.base + energies, 0, sizeof(double) * (size_t)n, s));
   int max_chunks = 1;
   int max_m = 1;
   for (int i = 0; i < n; ++i) {

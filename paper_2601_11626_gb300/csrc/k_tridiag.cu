@@ -8,9 +8,10 @@
 // needed: sigma~_j = sqrt(lambda_j) (Cor. 3), and the tail follows from the
 // trace, sum_{j > r_new} lambda_j = tr(T) - sum_{j <= r_new} lambda_j.
 //
-// One CTA per item, in three launch classes by core size: 4 warps (four CTAs
-// per SM) for n <= 192, 8 warps (two per SM) for n <= 320, 16 warps (one per
-// SM) above.  Each CTA owns its SM share of tensor memory (TMEM).
+// One CTA per item, in three launch classes by core size: 4 warps (four
+// CTAs per SM) for n <= 192, 8 warps (two per SM) for n <= 320, 16 warps
+// (one per SM) above.  Each CTA owns its SM share of tensor memory (TMEM).
+// Tiles are processed 8 columns at a time.
 //  1. G is assembled as 32 x 32 tiles of its lower tile triangle (diagonal
 //     tiles hold both halves), listed column by column.  The tiles consumed
 //     last -- revisited by the most steps -- live in TMEM (one tile per
@@ -55,6 +56,10 @@ struct ClassCfg {
   int warps, max_n;
 };
 constexpr ClassCfg kClass[3] = {{4, 192}, {8, 320}, {16, 1 << 30}};
+// CTAs per SM of each class (16 warps per SM at 128 registers a thread) and
+// the TMEM columns each CTA allocates (a power of two, the class's SM share).
+constexpr int kPerSm[3] = {4, 2, 1};
+constexpr int kTmemColsOf[3] = {128, 256, 512};
 
 __host__ __device__ __forceinline__ int tiles_in(int T) { return T * (T + 1) / 2; }
 // First list position of tile column b in a T-row lower tile triangle.
@@ -74,11 +79,11 @@ __host__ __device__ int smem_tile_cap(int smem_bytes, int n_max) {
   return avail > 0 ? (int)(avail / kTileFloats) : 0;
 }
 
-__host__ __device__ TileLayout tile_layout(int n, int warps, int smem_bytes, int n_max) {
+__host__ __device__ TileLayout tile_layout(int n, int tmem_cols, int smem_bytes, int n_max) {
   TileLayout L;
   L.T = (n + kTile - 1) / kTile;
   const int nt = tiles_in(L.T);
-  const int ct = 4 * warps;  // TMEM tiles: 32 columns per warp
+  const int ct = tmem_cols / 8;  // TMEM tiles: 4 lane quarters x (columns / 32)
   const int cap = ct + smem_tile_cap(smem_bytes, n_max);
   int g = 0;
   while (g < L.T && tiles_in(L.T - g) > cap) ++g;
@@ -173,102 +178,111 @@ __device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, f
       : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
 }
 
-// The per-element work of a tile whose row `lane` holds val[0..31]:
-// G -= vp wp^T + wp vp^T, then row sums (four partial chains) and column
-// sums, two columns per instruction.
-__device__ __forceinline__ float tile_update(float (&val)[32], float (&cp)[32], float vr, int a,
-                                             int b, int lane, const Step& st) {
+// Where row `lane` of a tile lives, moved 8 columns at a time.  Shared-memory
+// tiles are row-major with 16-byte chunks XOR-swizzled by row (element
+// (i, j) at 32 i + 4 ((j / 4) ^ (i % 8)) + j % 4), so a row moves with
+// conflict-free 128-bit accesses; global tiles are column-major (element
+// (i, j) at 32 j + i), one coalesced access per column; TMEM tiles hold row
+// i in lane i of the warp's quarter.
+struct SmemTile {
+  float* tp;
+  __device__ __forceinline__ void load8(int lane, int k8, float (&v)[8]) const {
+    const float4* rp = reinterpret_cast<const float4*>(tp + lane * kTile);
+    const float4 x = rp[(2 * k8) ^ (lane & 7)], y = rp[(2 * k8 + 1) ^ (lane & 7)];
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  }
+  __device__ __forceinline__ void store8(int lane, int k8, const float (&v)[8]) const {
+    float4* rp = reinterpret_cast<float4*>(tp + lane * kTile);
+    rp[(2 * k8) ^ (lane & 7)] = make_float4(v[0], v[1], v[2], v[3]);
+    rp[(2 * k8 + 1) ^ (lane & 7)] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+struct GlobTile {
+  float* tp;
+  __device__ __forceinline__ void load8(int lane, int k8, float (&v)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = tp[(8 * k8 + j) * kTile + lane];
+  }
+  __device__ __forceinline__ void store8(int lane, int k8, const float (&v)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tp[(8 * k8 + j) * kTile + lane] = v[j];
+  }
+};
+struct TmemTile {
+  uint32_t taddr;
+  __device__ __forceinline__ void load8(int, int k8, float (&v)[8]) const {
+    tmem_load8(taddr + 8u * k8, v);
+  }
+  __device__ __forceinline__ void store8(int, int k8, const float (&v)[8]) const {
+    tmem_store8(taddr + 8u * k8, v);
+  }
+};
+
+__device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
+  return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
+}
+
+// One tile, 8 columns at a time: G -= vp wp^T + wp vp^T, row sums (four
+// partial chains, added to p[row]) and column sums (kept in cp across the
+// tiles of a tile column), column s + 1 and G(n-1, n-1) copied out.
+template <class Tile>
+__device__ __forceinline__ void process_tile(const Tile& tl, int a, int b, int lane, const Step& st,
+                                             float (&cp)[32], float& pv) {
   const int r = a * kTile + lane;
+  const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
   const float nvp = -st.vprev[r], nwp = -st.wprev[r];
   const float colw = (a == b) ? 0.f : vr;  // diagonal tiles: row sums cover both halves
   const float4* vc4 = reinterpret_cast<const float4*>(st.vcur + b * kTile);
   const float4* vp4 = reinterpret_cast<const float4*>(st.vprev + b * kTile);
   const float4* wp4 = reinterpret_cast<const float4*>(st.wprev + b * kTile);
-  const int pq = (b == st.b0) ? st.ccn : -1;  // in-tile column holding v0
-  float ra0 = 0.f, ra1 = 0.f, ra2 = 0.f, ra3 = 0.f;
+  const bool col_next = b == st.b0;  // this tile column holds column s + 1 (and v0)
+  const bool diag_last = a == b && r == st.last_r;
+  float ra0 = 0.f, ra1 = 0.f, ra2 = 0.f, ra3 = 0.f, cx = 0.f, gx = 0.f;
 #pragma unroll
-  for (int q4 = 0; q4 < 8; ++q4) {
-    float4 vc = vc4[q4];
-    if ((pq >> 2) == q4) {
-      const int u = pq & 3;
-      vc.x = u == 0 ? st.v0 : vc.x;
-      vc.y = u == 1 ? st.v0 : vc.y;
-      vc.z = u == 2 ? st.v0 : vc.z;
-      vc.w = u == 3 ? st.v0 : vc.w;
+  for (int k8 = 0; k8 < 4; ++k8) {
+    float v[8];
+    tl.load8(lane, k8, v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q4 = 2 * k8 + h, c = 4 * q4, j = 4 * h;
+      float4 vc = vc4[q4];
+      if (col_next && (st.ccn >> 2) == q4) {
+        const int u = st.ccn & 3;
+        vc.x = u == 0 ? st.v0 : vc.x;
+        vc.y = u == 1 ? st.v0 : vc.y;
+        vc.z = u == 2 ? st.v0 : vc.z;
+        vc.w = u == 3 ? st.v0 : vc.w;
+      }
+      const float4 vp = vp4[q4], wp = wp4[q4];
+      fma2(v[j], v[j + 1], nwp, nwp, vp.x, vp.y, v[j], v[j + 1]);
+      fma2(v[j + 2], v[j + 3], nwp, nwp, vp.z, vp.w, v[j + 2], v[j + 3]);
+      fma2(v[j], v[j + 1], nvp, nvp, wp.x, wp.y, v[j], v[j + 1]);
+      fma2(v[j + 2], v[j + 3], nvp, nvp, wp.z, wp.w, v[j + 2], v[j + 3]);
+      fma2(ra0, ra1, v[j], v[j + 1], vc.x, vc.y, ra0, ra1);
+      fma2(ra2, ra3, v[j + 2], v[j + 3], vc.z, vc.w, ra2, ra3);
+      fma2(cp[c], cp[c + 1], v[j], v[j + 1], colw, colw, cp[c], cp[c + 1]);
+      fma2(cp[c + 2], cp[c + 3], v[j + 2], v[j + 3], colw, colw, cp[c + 2], cp[c + 3]);
     }
-    const float4 vp = vp4[q4], wp = wp4[q4];
-    const int c = q4 * 4;
-    float x0, x1, x2, x3;
-    fma2(x0, x1, nwp, nwp, vp.x, vp.y, val[c], val[c + 1]);
-    fma2(x2, x3, nwp, nwp, vp.z, vp.w, val[c + 2], val[c + 3]);
-    fma2(x0, x1, nvp, nvp, wp.x, wp.y, x0, x1);
-    fma2(x2, x3, nvp, nvp, wp.z, wp.w, x2, x3);
-    val[c] = x0;
-    val[c + 1] = x1;
-    val[c + 2] = x2;
-    val[c + 3] = x3;
-    fma2(ra0, ra1, x0, x1, vc.x, vc.y, ra0, ra1);
-    fma2(ra2, ra3, x2, x3, vc.z, vc.w, ra2, ra3);
-    fma2(cp[c], cp[c + 1], x0, x1, colw, colw, cp[c], cp[c + 1]);
-    fma2(cp[c + 2], cp[c + 3], x2, x3, colw, colw, cp[c + 2], cp[c + 3]);
-  }
-  return (ra0 + ra1) + (ra2 + ra3);
-}
-
-// Shared-memory tiles are row-major with 16-byte chunks XOR-swizzled by row
-// (element (i, j) at 32 i + 4 ((j / 4) ^ (i % 8)) + j % 4): lane i moves its
-// row with eight conflict-free 128-bit accesses.  Global tiles are
-// column-major (element (i, j) at 32 j + i): one coalesced access per column.
-template <bool kRowMajor>
-__device__ __forceinline__ void load_row(const float* tp, int lane, float (&val)[32]) {
-  if (kRowMajor) {
-    const float4* rp = reinterpret_cast<const float4*>(tp + lane * kTile);
+    tl.store8(lane, k8, v);
+    if (col_next) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 x = rp[q ^ (lane & 7)];
-      val[4 * q] = x.x;
-      val[4 * q + 1] = x.y;
-      val[4 * q + 2] = x.z;
-      val[4 * q + 3] = x.w;
+      for (int j = 0; j < 8; ++j) cx = (8 * k8 + j == st.ccn) ? v[j] : cx;
     }
-  } else {
+    if (diag_last) {
 #pragma unroll
-    for (int cc = 0; cc < 32; ++cc) val[cc] = tp[cc * kTile + lane];
+      for (int j = 0; j < 8; ++j) gx = (8 * k8 + j == (st.last_r & 31)) ? v[j] : gx;
+    }
   }
-}
-template <bool kRowMajor>
-__device__ __forceinline__ void store_row(float* tp, int lane, const float (&val)[32]) {
-  if (kRowMajor) {
-    float4* rp = reinterpret_cast<float4*>(tp + lane * kTile);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      rp[q ^ (lane & 7)] = make_float4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
-  } else {
-#pragma unroll
-    for (int cc = 0; cc < 32; ++cc) tp[cc * kTile + lane] = val[cc];
-  }
-}
-
-__device__ __forceinline__ float pick(const float (&val)[32], int cc) {
-  float x = 0.f;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) x = (i == cc) ? val[i] : x;
-  return x;
-}
-
-// Everything after the tile's values are final: column s + 1, the last
-// diagonal element, row sums.
-__device__ __forceinline__ void tile_finish(const float (&val)[32], float rowacc, float vr, int a,
-                                            int b, int lane, const Step& st, float& pv) {
-  const int r = a * kTile + lane;
-  if (b == st.b0) st.cnext[r] = pick(val, st.ccn);
-  if (a == b && r == st.last_r) *st.glast = pick(val, st.last_r & 31);
+  if (col_next) st.cnext[r] = cx;
+  if (diag_last) *st.glast = gx;
+  const float rowacc = (ra0 + ra1) + (ra2 + ra3);
   atomicAdd(&st.pcur[r], rowacc);
   pv = fmaf(rowacc, vr, pv);
 }
 
 // Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles.
-template <bool kRowMajor>
+template <class Tile>
 __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb, int T, int lane,
                                           const Step& st, float& pv) {
   if (La >= Lb) return;
@@ -278,14 +292,7 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
 #pragma unroll
   for (int q = 0; q < 32; ++q) cp[q] = 0.f;
   for (int L = La; L < Lb; ++L) {
-    float* tp = base + (int64_t)(L - Lbase) * kTileFloats;
-    float val[32];
-    load_row<kRowMajor>(tp, lane, val);
-    const int r = a * kTile + lane;
-    const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
-    const float rowacc = tile_update(val, cp, vr, a, b, lane, st);
-    store_row<kRowMajor>(tp, lane, val);
-    tile_finish(val, rowacc, vr, a, b, lane, st, pv);
+    process_tile(Tile{base + (int64_t)(L - Lbase) * kTileFloats}, a, b, lane, st, cp, pv);
     const int bb = b;
     tile_next(a, b, T);
     if (b != bb || L + 1 == Lb) flush_cols(cp, bb, lane, st, pv);
@@ -312,14 +319,7 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, i
 #pragma unroll
   for (int i = 0; i < 32; ++i) cp[i] = 0.f;
   for (int j = ja; j < jb; ++j) {
-    const uint32_t taddr = tq + tm_slot(t) * 32u;
-    float val[32];
-    tmem_load_tile(taddr, val);
-    const int r = a * kTile + lane;
-    const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
-    const float rowacc = tile_update(val, cp, vr, a, b, lane, st);
-    tmem_store_tile(taddr, val);
-    tile_finish(val, rowacc, vr, a, b, lane, st, pv);
+    process_tile(TmemTile{tq + tm_slot(t) * 32u}, a, b, lane, st, cp, pv);
     const int bb = b;
     const int adv = (j & 1) ? 7 : 1;  // to the quarter's next tile
     for (int u = 0; u < adv; ++u) tile_next(a, b, T);
@@ -328,12 +328,27 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, i
   }
 }
 
-template <int kWarps>
-__global__ void __launch_bounds__(kWarps * 32, 16 / kWarps)
+// Assemble tile (a, b) of G into its place, 8 columns at a time.
+template <class Tile>
+__device__ __forceinline__ void assemble_tile(const Tile& tl, const CoreDesc& d, int n, int a,
+                                              int b, int lane) {
+  const int r = a * kTile + lane;
+#pragma unroll
+  for (int k8 = 0; k8 < 4; ++k8) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = core_gram(d, n, r, b * kTile + 8 * k8 + j);
+    tl.store8(lane, k8, v);
+  }
+}
+
+template <int kCls>
+__global__ void __launch_bounds__(kClass[kCls].warps * 32, kPerSm[kCls])
 core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_max,
                     int* __restrict__ status) {
+  constexpr int kWarps = kClass[kCls].warps;
   constexpr int kThreads = kWarps * 32;
-  constexpr uint32_t kTmemCols = 32u * kWarps;
+  constexpr uint32_t kTmemCols = kTmemColsOf[kCls];
   extern __shared__ __align__(16) float smem[];
   const CoreDesc d = descs[blockIdx.x];
   const int n = d.rt + d.k;
@@ -350,7 +365,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   float* cb1 = ev + 7 * npad;
   float* red = ev + 8 * npad;  // kRed: per-warp partial sums
   float* tsm = red + kRed;     // shared-memory tiles
-  const TileLayout Lay = tile_layout(n, kWarps, smem_bytes, n_max);
+  const TileLayout Lay = tile_layout(n, kTmemCols, smem_bytes, n_max);
   const int T = Lay.T;
   __shared__ uint32_t s_tmem;
   __shared__ float s_glast;
@@ -368,12 +383,8 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   for (int L = wid; L < Lay.Lt; L += kWarps) {
     int a, b;
     tile_of(L, T, a, b);
-    const int r = a * kTile + lane;
-    float val[32];
-#pragma unroll
-    for (int cc = 0; cc < 32; ++cc) val[cc] = core_gram(d, n, r, b * kTile + cc);
-    if (L < Lay.Lg) store_row<false>(d.work + (int64_t)L * kTileFloats, lane, val);
-    else store_row<true>(tsm + (int64_t)(L - Lay.Lg) * kTileFloats, lane, val);
+    if (L < Lay.Lg) assemble_tile(GlobTile{d.work + (int64_t)L * kTileFloats}, d, n, a, b, lane);
+    else assemble_tile(SmemTile{tsm + (int64_t)(L - Lay.Lg) * kTileFloats}, d, n, a, b, lane);
   }
   for (int i = tid; i < npad; i += kThreads) {
     vb0[i] = 0.f;
@@ -408,11 +419,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       if (t >= Lay.Ntm) break;
       int a, b;
       tile_of(Lay.Lt + t, T, a, b);
-      const int r = a * kTile + lane;
-      float val[32];
-#pragma unroll
-      for (int cc = 0; cc < 32; ++cc) val[cc] = core_gram(d, n, r, b * kTile + cc);
-      tmem_store_tile(tq + tm_slot(t) * 32u, val);
+      assemble_tile(TmemTile{tq + tm_slot(t) * 32u}, d, n, a, b, lane);
     }
     tmem_wait_st();
     tmem_fence_before();
@@ -546,13 +553,13 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       const Step st{vcur, vprev, wv, pcur, cnext, &s_glast, b0, (s + 1) & 31, s + 1, n - 1, v0};
       const int g_lo = as_glo, g_hi = as_ghi;
       float pv = 0.f;
-      if ((wid & 1) == 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
-      mem_tiles<true>(tsm, Lay.Lg, as_slo, as_shi, T, lane, st, pv);
+      if ((wid & 1) == 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
+      mem_tiles<SmemTile>(tsm, Lay.Lg, as_slo, as_shi, T, lane, st, pv);
       if (use_tmem) {
         tmem_tiles(tq, Lay.Lt, wid & 3, as_ja, as_jb, T, lane, st, pv);
         tmem_wait_st();
       }
-      if ((wid & 1) != 0) mem_tiles<false>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
+      if ((wid & 1) != 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
       pv = warp_sum(pv);
       if (lane == 0) pvred[wid] = pv;
     }
@@ -681,29 +688,29 @@ int tridiag_smem_bytes(int cls, int n_max) {
   const int share = (cls == 0) ? 56 * 1024 : 112 * 1024;
   const int npad = (n_max + kTile - 1) / kTile * kTile;
   const int T = npad / kTile;
-  const int need_tiles = max(0, tiles_in(T) - 4 * kClass[cls].warps);
+  const int need_tiles = max(0, tiles_in(T) - kTmemColsOf[cls] / 8);
   const int need = (kVecs * npad + kRed + need_tiles * kTileFloats) * 4;
   return min(need, share);
 }
 
 int64_t tridiag_work_floats(int cls, int n, int n_max) {
-  return (int64_t)tile_layout(n, kClass[cls].warps, tridiag_smem_bytes(cls, n_max), n_max).Lg *
+  return (int64_t)tile_layout(n, kTmemColsOf[cls], tridiag_smem_bytes(cls, n_max), n_max).Lg *
          kTileFloats;
 }
 
-template <int kWarps>
+template <int kCls>
 static cudaError_t launch_class(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
                                 int* d_status, cudaStream_t s) {
   if (smem_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel<kWarps>,
+    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel<kCls>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
   }
   prof_begin(s);
-  core_tridiag_kernel<kWarps><<<n_items, kWarps * 32, smem_bytes, s>>>(d_desc, smem_bytes, n_max,
-                                                                        d_status);
-  prof_end(kWarps == 4 ? "core_tridiag.small" : kWarps == 8 ? "core_tridiag.medium"
-                                                            : "core_tridiag.large", s);
+  core_tridiag_kernel<kCls><<<n_items, kClass[kCls].warps * 32, smem_bytes, s>>>(
+      d_desc, smem_bytes, n_max, d_status);
+  prof_end(kCls == 0 ? "core_tridiag.small" : kCls == 1 ? "core_tridiag.medium"
+                                                        : "core_tridiag.large", s);
   return cudaGetLastError();
 }
 
@@ -711,9 +718,9 @@ cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, in
                                 int* d_status, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   const int smem = tridiag_smem_bytes(cls, n_max);
-  if (cls == 0) return launch_class<4>(d_desc, n_items, smem, n_max, d_status, s);
-  if (cls == 1) return launch_class<8>(d_desc, n_items, smem, n_max, d_status, s);
-  return launch_class<16>(d_desc, n_items, smem, n_max, d_status, s);
+  if (cls == 0) return launch_class<0>(d_desc, n_items, smem, n_max, d_status, s);
+  if (cls == 1) return launch_class<1>(d_desc, n_items, smem, n_max, d_status, s);
+  return launch_class<2>(d_desc, n_items, smem, n_max, d_status, s);
 }
 
 }  // namespace csvd

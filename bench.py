@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--n-states", type=int, default=64)
     ap.add_argument("--per-state", type=int, default=64)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parity-samples", type=int, default=8)
@@ -320,35 +320,81 @@ def main():
                  "accept_agree": bool((pb.accept == batch.accept).all())}
         del pb
 
-    # end to end through the public API: inputs from pinned host memory
+    # end to end through the public API: every step copies its inputs from
+    # pinned host memory and reads its results back; the copy of step i runs
+    # on a second stream into the other of two device pools while step i - 1
+    # is scored (double buffering)
     e2e = None
     if args.e2e_steps > 0:
         pool = w["pools"][1]
         host = torch.empty(pool.shape, dtype=pool.dtype, pin_memory=True)
         host.copy_(pool)
+        pools = [pool, torch.empty_like(pool)]
+
+        def views(p):
+            out = []
+            for c in cands:
+                off = (c.data_ptr() - pool.data_ptr()) // pool.element_size()
+                ld = c.stride(0)
+                out.append(p[off:off + m * ld].view(m, ld)[:, :c.shape[1]])
+            return out
+
+        batches = [batch, csvd.ScoreBatch(states, w["cand_state"], views(pools[1]), eps,
+                                          args.precision)]
         out_bytes = batch.tail.numel() * 8 + batch.accept.numel() + batch.sigma.numel() * 4
-        o_tail = torch.empty(batch.tail.shape, dtype=batch.tail.dtype, pin_memory=True)
-        o_acc = torch.empty(batch.accept.shape, dtype=batch.accept.dtype, pin_memory=True)
-        o_sig = torch.empty(batch.sigma.shape, dtype=batch.sigma.dtype, pin_memory=True)
+        outs = [(torch.empty(batch.tail.shape, dtype=batch.tail.dtype, pin_memory=True),
+                 torch.empty(batch.accept.shape, dtype=batch.accept.dtype, pin_memory=True),
+                 torch.empty(batch.sigma.shape, dtype=batch.sigma.dtype, pin_memory=True))
+                for _ in range(2)]
+        copy_stream = torch.cuda.Stream()
+        # one copy with nothing else running, for reference
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(copy_stream):
+            a0.record(copy_stream)
+            pools[1].copy_(host, non_blocking=True)
+            a1.record(copy_stream)
+        a1.synchronize()
+        alone_ms = a0.elapsed_time(a1)
+        ready = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        c0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
+        c1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps)]
         barrier()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)
-        for _ in range(args.e2e_steps):
-            pool.copy_(host, non_blocking=True)
-            batch.run()
-            o_tail.copy_(batch.tail, non_blocking=True)
-            o_acc.copy_(batch.accept, non_blocking=True)
-            o_sig.copy_(batch.sigma, non_blocking=True)
+        for e in done:
+            e.record(stream)
+        for i in range(args.e2e_steps):
+            b = i % 2
+            copy_stream.wait_event(done[b])
+            with torch.cuda.stream(copy_stream):
+                c0[i].record(copy_stream)
+                pools[b].copy_(host, non_blocking=True)
+                c1[i].record(copy_stream)
+                ready[b].record(copy_stream)
+            stream.wait_event(ready[b])
+            batches[b].run()
+            for o, src in zip(outs[b], (batches[b].tail, batches[b].accept, batches[b].sigma)):
+                o.copy_(src, non_blocking=True)
+            done[b].record(stream)
         q1.record(stream)
         q1.synchronize()
         qms = q0.elapsed_time(q1) / args.e2e_steps
+        h2d_ms = sum(a.elapsed_time(z) for a, z in zip(c0, c1)) / args.e2e_steps
         if world > 1:
             t = torch.tensor([qms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             qms = float(t)
+        in_bytes = pool.numel() * pool.element_size()
         e2e = {"value": world * n / (qms / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": pool.numel() * pool.element_size(),
-               "d2h_bytes_per_step": out_bytes, "ms_per_step": qms, "steps": args.e2e_steps}
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
+               "ms_per_step": qms, "steps": args.e2e_steps,
+               "h2d_gbs": in_bytes / (h2d_ms / 1000.0) / 1e9,
+               "h2d_gbs_alone": in_bytes / (alone_ms / 1000.0) / 1e9,
+               "h2d_ms_each": [round(a.elapsed_time(z), 2) for a, z in zip(c0, c1)],
+               "overlap": "inputs of step i copied on a second stream while step i-1 is scored"}
+        del batches, pools
 
     # sampled parity against the FP64 oracle from the states the GPU used
     parity = None

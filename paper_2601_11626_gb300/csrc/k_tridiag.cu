@@ -134,8 +134,8 @@ __device__ __forceinline__ int sturm_count(const float* dv, const float* e2, int
   return cnt;
 }
 
-// Vectors of one main pass.  v_s[s+1] (= v0) is patched in registers: the
-// shared copy is written concurrently by every warp.
+// Vectors of one main pass.  Every warp writes v_s[s+1] (= v0, the same
+// value) into the shared vector itself before it reads it.
 struct Step {
   const float* vcur;   // v of this step
   const float* vprev;  // pending update: v and w of the previous step
@@ -148,35 +148,30 @@ struct Step {
   float v0;
 };
 
-// Lane L ends with the sum over lanes of cp[L]; added to p[32 b + L].
-__device__ __forceinline__ void flush_cols(float (&cp)[32], int b, int lane, const Step& st,
+// Column-sum accumulators: cp[i] holds columns 2i and 2i + 1 of a tile column.
+#define CP(k) ((k) & 1 ? cp[(k) >> 1].y : cp[(k) >> 1].x)
+
+// Lane L ends with the sum over lanes of column L's accumulator; added to
+// p[32 b + L].
+__device__ __forceinline__ void flush_cols(float2 (&cp)[16], int b, int lane, const Step& st,
                                            float& pv) {
 #pragma unroll
   for (int sh = 16; sh >= 1; sh >>= 1) {
 #pragma unroll
     for (int i = 0; i < sh; ++i) {
       const bool up = (lane & sh) != 0;
-      const float send = up ? cp[i] : cp[i + sh];
-      const float keep = up ? cp[i + sh] : cp[i];
-      cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+      const float send = up ? CP(i) : CP(i + sh);
+      const float keep = up ? CP(i + sh) : CP(i);
+      CP(i) = keep + __shfl_xor_sync(0xffffffffu, send, sh);
     }
   }
   const int c = b * kTile + lane;
-  const float vc = (c == st.s1) ? st.v0 : st.vcur[c];
-  atomicAdd(&st.pcur[c], cp[0]);
-  pv = fmaf(cp[0], vc, pv);
+  atomicAdd(&st.pcur[c], cp[0].x);
+  pv = fmaf(cp[0].x, st.vcur[c], pv);
 #pragma unroll
-  for (int q = 0; q < 32; ++q) cp[q] = 0.f;
+  for (int q = 0; q < 16; ++q) cp[q] = make_float2(0.f, 0.f);
 }
-
-// Two independent single-rounding FMAs in one instruction (packed f32x2).
-__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1,
-                                     float c0, float c1) {
-  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
-      : "=f"(d0), "=f"(d1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
-}
+#undef CP
 
 // Where row `lane` of a tile lives, moved 8 columns at a time.  Shared-memory
 // tiles are row-major with 16-byte chunks XOR-swizzled by row (element
@@ -186,36 +181,46 @@ __device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, f
 // i in lane i of the warp's quarter.
 struct SmemTile {
   float* tp;
-  __device__ __forceinline__ void load8(int lane, int k8, float (&v)[8]) const {
+  __device__ __forceinline__ void load8(int lane, int k8, float2 (&v)[4]) const {
     const float4* rp = reinterpret_cast<const float4*>(tp + lane * kTile);
     const float4 x = rp[(2 * k8) ^ (lane & 7)], y = rp[(2 * k8 + 1) ^ (lane & 7)];
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    v[0] = make_float2(x.x, x.y);
+    v[1] = make_float2(x.z, x.w);
+    v[2] = make_float2(y.x, y.y);
+    v[3] = make_float2(y.z, y.w);
   }
-  __device__ __forceinline__ void store8(int lane, int k8, const float (&v)[8]) const {
+  __device__ __forceinline__ void store8(int lane, int k8, const float2 (&v)[4]) const {
     float4* rp = reinterpret_cast<float4*>(tp + lane * kTile);
-    rp[(2 * k8) ^ (lane & 7)] = make_float4(v[0], v[1], v[2], v[3]);
-    rp[(2 * k8 + 1) ^ (lane & 7)] = make_float4(v[4], v[5], v[6], v[7]);
+    rp[(2 * k8) ^ (lane & 7)] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    rp[(2 * k8 + 1) ^ (lane & 7)] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
   }
 };
 struct GlobTile {
   float* tp;
-  __device__ __forceinline__ void load8(int lane, int k8, float (&v)[8]) const {
+  __device__ __forceinline__ void load8(int lane, int k8, float2 (&v)[4]) const {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = tp[(8 * k8 + j) * kTile + lane];
+    for (int j = 0; j < 4; ++j)
+      v[j] = make_float2(tp[(8 * k8 + 2 * j) * kTile + lane], tp[(8 * k8 + 2 * j + 1) * kTile + lane]);
   }
-  __device__ __forceinline__ void store8(int lane, int k8, const float (&v)[8]) const {
+  __device__ __forceinline__ void store8(int lane, int k8, const float2 (&v)[4]) const {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) tp[(8 * k8 + j) * kTile + lane] = v[j];
+    for (int j = 0; j < 4; ++j) {
+      tp[(8 * k8 + 2 * j) * kTile + lane] = v[j].x;
+      tp[(8 * k8 + 2 * j + 1) * kTile + lane] = v[j].y;
+    }
   }
 };
 struct TmemTile {
   uint32_t taddr;
-  __device__ __forceinline__ void load8(int, int k8, float (&v)[8]) const {
-    tmem_load8(taddr + 8u * k8, v);
+  __device__ __forceinline__ void load8(int, int k8, float2 (&v)[4]) const {
+    float x[8];
+    tmem_load8(taddr + 8u * k8, x);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = make_float2(x[2 * j], x[2 * j + 1]);
   }
-  __device__ __forceinline__ void store8(int, int k8, const float (&v)[8]) const {
-    tmem_store8(taddr + 8u * k8, v);
+  __device__ __forceinline__ void store8(int, int k8, const float2 (&v)[4]) const {
+    const float x[8] = {v[0].x, v[0].y, v[1].x, v[1].y, v[2].x, v[2].y, v[3].x, v[3].y};
+    tmem_store8(taddr + 8u * k8, x);
   }
 };
 
@@ -223,79 +228,115 @@ __device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
   return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
 }
 
-// One tile, 8 columns at a time: G -= vp wp^T + wp vp^T, row sums (four
-// partial chains, added to p[row]) and column sums (kept in cp across the
-// tiles of a tile column), column s + 1 and G(n-1, n-1) copied out.
-template <class Tile>
-__device__ __forceinline__ void process_tile(const Tile& tl, int a, int b, int lane, const Step& st,
-                                             float (&cp)[32], float& pv) {
-  const int r = a * kTile + lane;
-  const float vr = (r == st.s1) ? st.v0 : st.vcur[r];
-  const float nvp = -st.vprev[r], nwp = -st.wprev[r];
-  const float colw = (a == b) ? 0.f : vr;  // diagonal tiles: row sums cover both halves
+// K tiles of one tile column b (rows a, a + 1, ...), 8 columns at a time:
+// G -= vp wp^T + wp vp^T, row sums (two partial chains per tile, added to
+// p[row]) and column sums (kept in cp across the tiles of the column),
+// column s + 1 and G(n-1, n-1) copied out.  Pairs of columns go through
+// packed f32x2 FMAs; the column vectors are loaded once for the K tiles.
+template <int K, class Tile>
+__device__ __forceinline__ void process_tiles(const Tile (&tl)[K], int a, int b, int lane,
+                                              const Step& st, float2 (&cp)[16], float& pv) {
+  float vr[K], cx[K], gx[K];
+  float2 nvp[K], nwp[K], colw[K], ra[K];
+  bool last_tile[K];  // the diagonal tile holding G(n-1, n-1): same in every lane
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int r = (a + t) * kTile + lane;
+    vr[t] = st.vcur[r];
+    const float p = -st.vprev[r], w = -st.wprev[r];
+    nvp[t] = make_float2(p, p);
+    nwp[t] = make_float2(w, w);
+    const float cw = (a + t == b) ? 0.f : vr[t];  // diagonal tiles: row sums cover both halves
+    colw[t] = make_float2(cw, cw);
+    ra[t] = make_float2(0.f, 0.f);
+    cx[t] = gx[t] = 0.f;
+    last_tile[t] = a + t == b && b == (st.last_r >> 5);
+  }
   const float4* vc4 = reinterpret_cast<const float4*>(st.vcur + b * kTile);
   const float4* vp4 = reinterpret_cast<const float4*>(st.vprev + b * kTile);
   const float4* wp4 = reinterpret_cast<const float4*>(st.wprev + b * kTile);
-  const bool col_next = b == st.b0;  // this tile column holds column s + 1 (and v0)
-  const bool diag_last = a == b && r == st.last_r;
-  float ra0 = 0.f, ra1 = 0.f, ra2 = 0.f, ra3 = 0.f, cx = 0.f, gx = 0.f;
+  const bool col_next = b == st.b0;  // this tile column holds column s + 1
 #pragma unroll
   for (int k8 = 0; k8 < 4; ++k8) {
-    float v[8];
-    tl.load8(lane, k8, v);
+    float2 v[K][4];
+#pragma unroll
+    for (int t = 0; t < K; ++t) tl[t].load8(lane, k8, v[t]);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int q4 = 2 * k8 + h, c = 4 * q4, j = 4 * h;
-      float4 vc = vc4[q4];
-      if (col_next && (st.ccn >> 2) == q4) {
-        const int u = st.ccn & 3;
-        vc.x = u == 0 ? st.v0 : vc.x;
-        vc.y = u == 1 ? st.v0 : vc.y;
-        vc.z = u == 2 ? st.v0 : vc.z;
-        vc.w = u == 3 ? st.v0 : vc.w;
+      const int q4 = 2 * k8 + h;
+      const float4 vc = vc4[q4], vp = vp4[q4], wp = wp4[q4];
+      const float2 vc0 = make_float2(vc.x, vc.y), vc1 = make_float2(vc.z, vc.w);
+      const float2 vp0 = make_float2(vp.x, vp.y), vp1 = make_float2(vp.z, vp.w);
+      const float2 wp0 = make_float2(wp.x, wp.y), wp1 = make_float2(wp.z, wp.w);
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        float2 x0 = v[t][2 * h], x1 = v[t][2 * h + 1];
+        x0 = __ffma2_rn(nwp[t], vp0, x0);
+        x1 = __ffma2_rn(nwp[t], vp1, x1);
+        x0 = __ffma2_rn(nvp[t], wp0, x0);
+        x1 = __ffma2_rn(nvp[t], wp1, x1);
+        v[t][2 * h] = x0;
+        v[t][2 * h + 1] = x1;
+        ra[t] = __ffma2_rn(x0, vc0, ra[t]);
+        ra[t] = __ffma2_rn(x1, vc1, ra[t]);
+        cp[2 * q4] = __ffma2_rn(x0, colw[t], cp[2 * q4]);
+        cp[2 * q4 + 1] = __ffma2_rn(x1, colw[t], cp[2 * q4 + 1]);
       }
-      const float4 vp = vp4[q4], wp = wp4[q4];
-      fma2(v[j], v[j + 1], nwp, nwp, vp.x, vp.y, v[j], v[j + 1]);
-      fma2(v[j + 2], v[j + 3], nwp, nwp, vp.z, vp.w, v[j + 2], v[j + 3]);
-      fma2(v[j], v[j + 1], nvp, nvp, wp.x, wp.y, v[j], v[j + 1]);
-      fma2(v[j + 2], v[j + 3], nvp, nvp, wp.z, wp.w, v[j + 2], v[j + 3]);
-      fma2(ra0, ra1, v[j], v[j + 1], vc.x, vc.y, ra0, ra1);
-      fma2(ra2, ra3, v[j + 2], v[j + 3], vc.z, vc.w, ra2, ra3);
-      fma2(cp[c], cp[c + 1], v[j], v[j + 1], colw, colw, cp[c], cp[c + 1]);
-      fma2(cp[c + 2], cp[c + 3], v[j + 2], v[j + 3], colw, colw, cp[c + 2], cp[c + 3]);
     }
-    tl.store8(lane, k8, v);
-    if (col_next) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) cx = (8 * k8 + j == st.ccn) ? v[j] : cx;
-    }
-    if (diag_last) {
+    for (int t = 0; t < K; ++t) {
+      tl[t].store8(lane, k8, v[t]);
+      if (col_next) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) gx = (8 * k8 + j == (st.last_r & 31)) ? v[j] : gx;
+        for (int j = 0; j < 8; ++j)
+          cx[t] = (8 * k8 + j == st.ccn) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x) : cx[t];
+      }
+      if (last_tile[t]) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          gx[t] = (8 * k8 + j == (st.last_r & 31)) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x)
+                                                   : gx[t];
+      }
     }
   }
-  if (col_next) st.cnext[r] = cx;
-  if (diag_last) *st.glast = gx;
-  const float rowacc = (ra0 + ra1) + (ra2 + ra3);
-  atomicAdd(&st.pcur[r], rowacc);
-  pv = fmaf(rowacc, vr, pv);
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int r = (a + t) * kTile + lane;
+    if (col_next) st.cnext[r] = cx[t];
+    if (last_tile[t] && r == st.last_r) *st.glast = gx[t];
+    const float rowacc = ra[t].x + ra[t].y;
+    atomicAdd(&st.pcur[r], rowacc);
+    pv = fmaf(rowacc, vr[t], pv);
+  }
 }
 
-// Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles.
+// Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles;
+// two at a time while they share a tile column.
 template <class Tile>
 __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb, int T, int lane,
                                           const Step& st, float& pv) {
   if (La >= Lb) return;
   int a, b;
   tile_of(La, T, a, b);
-  float cp[32];
+  float2 cp[16];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) cp[q] = 0.f;
-  for (int L = La; L < Lb; ++L) {
-    process_tile(Tile{base + (int64_t)(L - Lbase) * kTileFloats}, a, b, lane, st, cp, pv);
+  for (int q = 0; q < 16; ++q) cp[q] = make_float2(0.f, 0.f);
+  for (int L = La; L < Lb;) {
+    int used;
+    if (L + 1 < Lb && a + 1 < T) {
+      const Tile tl[2] = {Tile{base + (int64_t)(L - Lbase) * kTileFloats},
+                          Tile{base + (int64_t)(L + 1 - Lbase) * kTileFloats}};
+      process_tiles<2>(tl, a, b, lane, st, cp, pv);
+      used = 2;
+    } else {
+      const Tile tl[1] = {Tile{base + (int64_t)(L - Lbase) * kTileFloats}};
+      process_tiles<1>(tl, a, b, lane, st, cp, pv);
+      used = 1;
+    }
+    L += used;
     const int bb = b;
-    tile_next(a, b, T);
-    if (b != bb || L + 1 == Lb) flush_cols(cp, bb, lane, st, pv);
+    for (int u = 0; u < used; ++u) tile_next(a, b, T);
+    if (b != bb || L >= Lb) flush_cols(cp, bb, lane, st, pv);
   }
 }
 
@@ -315,16 +356,27 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, i
   int t = tm_tile(q, ja);
   int a, b;
   tile_of(Lt + t, T, a, b);
-  float cp[32];
+  float2 cp[16];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) cp[i] = 0.f;
-  for (int j = ja; j < jb; ++j) {
-    process_tile(TmemTile{tq + tm_slot(t) * 32u}, a, b, lane, st, cp, pv);
+  for (int i = 0; i < 16; ++i) cp[i] = make_float2(0.f, 0.f);
+  for (int j = ja; j < jb;) {
+    int adv;  // list positions to the quarter's next unprocessed tile
+    if ((j & 1) == 0 && j + 1 < jb && a + 1 < T) {
+      // tiles t and t + 1: one pair, consecutive rows of one tile column
+      const TmemTile tl[2] = {TmemTile{tq + tm_slot(t) * 32u}, TmemTile{tq + tm_slot(t + 1) * 32u}};
+      process_tiles<2>(tl, a, b, lane, st, cp, pv);
+      j += 2;
+      adv = 8;
+    } else {
+      const TmemTile tl[1] = {TmemTile{tq + tm_slot(t) * 32u}};
+      process_tiles<1>(tl, a, b, lane, st, cp, pv);
+      adv = (j & 1) ? 7 : 1;
+      j += 1;
+    }
     const int bb = b;
-    const int adv = (j & 1) ? 7 : 1;  // to the quarter's next tile
     for (int u = 0; u < adv; ++u) tile_next(a, b, T);
     t += adv;
-    if (b != bb || j + 1 == jb) flush_cols(cp, bb, lane, st, pv);
+    if (b != bb || j >= jb) flush_cols(cp, bb, lane, st, pv);
   }
 }
 
@@ -335,9 +387,11 @@ __device__ __forceinline__ void assemble_tile(const Tile& tl, const CoreDesc& d,
   const int r = a * kTile + lane;
 #pragma unroll
   for (int k8 = 0; k8 < 4; ++k8) {
-    float v[8];
+    float2 v[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = core_gram(d, n, r, b * kTile + 8 * k8 + j);
+    for (int j = 0; j < 4; ++j)
+      v[j] = make_float2(core_gram(d, n, r, b * kTile + 8 * k8 + 2 * j),
+                         core_gram(d, n, r, b * kTile + 8 * k8 + 2 * j + 1));
     tl.store8(lane, k8, v);
   }
 }

@@ -74,14 +74,18 @@ __device__ __forceinline__ void tmem_store_tile(uint32_t taddr, const float* v) 
 }
 
 // 8-column variants: lane i <-> columns [col, col + 8) of TMEM lane base + i.
+// The load waits for itself inside the same statement, so its outputs exist
+// only once they are valid; neither touches generic memory, so the compiler
+// may move shared- or global-memory accesses across them (the relative order
+// of tcgen05 statements, fences and barriers is kept: all are volatile).
 __device__ __forceinline__ void tmem_load8(uint32_t taddr, float* v) {
   uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -89,8 +93,7 @@ __device__ __forceinline__ void tmem_store8(uint32_t taddr, const float* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
                "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-               : "memory");
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
 }
 
 }  // namespace csvd

@@ -111,6 +111,15 @@ __device__ __forceinline__ void tile_next(int& a, int& b, int T) {
   }
 }
 
+// Move k >= 0 positions forward in the column-major tile list.
+__device__ __forceinline__ void tile_skip(int& a, int& b, int T, int k) {
+  a += k;
+  while (a >= T && b + 1 < T) {  // column b has rows b .. T-1
+    a -= T - (b + 1);
+    ++b;
+  }
+}
+
 // Element (r, c) of G (zero outside n x n).
 __device__ __forceinline__ float core_gram(const CoreDesc& d, int n, int r, int c) {
   if (r >= n || c >= n) return 0.f;
@@ -335,7 +344,7 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
     }
     L += used;
     const int bb = b;
-    for (int u = 0; u < used; ++u) tile_next(a, b, T);
+    tile_skip(a, b, T, used);
     if (b != bb || L >= Lb) flush_cols(cp, bb, lane, st, pv);
   }
 }
@@ -374,7 +383,7 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, i
       j += 1;
     }
     const int bb = b;
-    for (int u = 0; u < adv; ++u) tile_next(a, b, T);
+    tile_skip(a, b, T, adv);
     t += adv;
     if (b != bb || j >= jb) flush_cols(cp, bb, lane, st, pv);
   }

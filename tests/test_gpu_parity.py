@@ -136,6 +136,31 @@ def test_score_uneven_large_cores(csvd, precision):
     _compare_scores(csvd, gst, cst, w["cand_state"], cands, 0.25, precision)
 
 
+def test_score_eigen_core_layout_boundaries(csvd):
+    """Widths that put the core size n = r_t + k on every edge of the
+    mixed-form eigen core's layouts: the launch classes (n <= 192, <= 320,
+    larger), the last core held wholly on-chip (448) and the first with a
+    global tile column (449), the largest (576), single-tile and one-row
+    cores, and ragged tile tails on both sides of each edge."""
+    w = synth.scoring_c4(r=64, n_states=1, appends=3, per_state=1, device="cuda")
+    m, r = w["m"], w["r"]
+    cst = _oracle_states(m, r, w["states"])
+    gst = [_load(csvd, c) for c in cst]
+    rt = int(gst[0].rank)
+    assert rt == 64
+    ns = [65, 66, 95, 96, 97, 160, 191, 192, 193, 224, 225, 319, 320, 321, 447, 448, 449, 480,
+          481, 575, 576]
+    widths = [n - rt for n in ns]
+    raw = synth.random_blocks(m, widths, seed=21, decay=0.95, device="cuda")
+    # energies comparable to the state's, so that every tail stays a few
+    # percent of ||M||^2 (the mixed form's tail floor is ~1e-6 ||M||^2)
+    raw = [b * math.sqrt(2000.0 / float((b.double() ** 2).sum())) for b in raw]
+    blocks = synth.pack_blocks(raw, ld_align=8)[0]
+    # mix in latent-subspace blocks so that some merges are accepted
+    blocks = list(blocks) + list(w["candidates"])
+    _compare_scores(csvd, gst, cst, [0] * len(blocks), blocks, 0.25, "mixed")
+
+
 def test_score_simt_and_tensor_gram_agree(csvd):
     """The same candidates through the tensor-core Gram (16-byte aligned rows)
     and the SIMT fallback (odd leading dimension) against the oracle."""

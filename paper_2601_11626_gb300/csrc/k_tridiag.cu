@@ -322,11 +322,9 @@ __device__ __forceinline__ void process_tiles(const Tile (&tl)[K], int a, int b,
 // Tiles at list positions [La, Lb), stored at base + (L - Lbase) tiles;
 // two at a time while they share a tile column.
 template <class Tile>
-__device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb, int T, int lane,
-                                          const Step& st, float& pv) {
+__device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb, int a, int b,
+                                          int T, int lane, const Step& st, float& pv) {
   if (La >= Lb) return;
-  int a, b;
-  tile_of(La, T, a, b);
   float2 cp[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) cp[q] = make_float2(0.f, 0.f);
@@ -359,12 +357,10 @@ __device__ __forceinline__ int tm_count(int q, int t) {
 __device__ __forceinline__ uint32_t tm_slot(int t) { return (uint32_t)(((t >> 3) << 1) | (t & 1)); }
 
 // The warp's TMEM tiles: quarter q's tiles j in [ja, jb), at positions Lt + t.
-__device__ __forceinline__ void tmem_tiles(uint32_t tq, int Lt, int q, int ja, int jb, int T,
-                                           int lane, const Step& st, float& pv) {
+__device__ __forceinline__ void tmem_tiles(uint32_t tq, int q, int ja, int jb, int a, int b,
+                                           int T, int lane, const Step& st, float& pv) {
   if (ja >= jb) return;
   int t = tm_tile(q, ja);
-  int a, b;
-  tile_of(Lt + t, T, a, b);
   float2 cp[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) cp[i] = make_float2(0.f, 0.f);
@@ -495,6 +491,8 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   // 2. tridiagonalisation (see the file comment for the two phases)
   float tau_prev = 0.f;  // tau of the pending reflector (same in every thread)
   int as_glo = 0, as_ghi = 0, as_slo = 0, as_shi = 0, as_ja = 0, as_jb = 0;  // the warp's share
+  int ga = 0, gb = 0, sa = 0, sb = 0, ta = 0, tb = 0;  // and the first tile of each part
+  const int Nt = tiles_in(T);
   for (int s = 0;; ++s) {
     const bool odd = (s & 1) != 0;
     float* vcur = odd ? vb1 : vb0;
@@ -506,9 +504,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     const bool last = s + 2 >= n;
     const int b0 = (s + 1) >> 5;
     {
-      float pvs = 0.f;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) pvs += pvred[w];
+      const float pvs = warp_sum(lane < kWarps ? pvred[lane] : 0.f);
       const float kk = (s >= 1) ? 0.5f * tau_prev * tau_prev * pvs : 0.f;
       const float vs = vprev[s];
       const float ws = (s >= 1) ? fmaf(tau_prev, pprev[s], -kk * vs) : 0.f;
@@ -532,9 +528,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       if (lane == 0) red[wid] = part;
     }
     __syncthreads();
-    float tail2 = 0.f;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) tail2 += red[w];
+    const float tail2 = warp_sum(lane < kWarps ? red[lane] : 0.f);  // the same in every lane
     if (last) {
       if (tid == 0) {
         if (n >= 2) {
@@ -611,18 +605,22 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       // global tiles: an even share each; half the warps take them first
       as_glo = L0 + ng * wid / kWarps;
       as_ghi = L0 + ng * (wid + 1) / kWarps;
+      // first tile of each share (unchanged until b0 moves)
+      tile_of(min(as_glo, Nt - 1), T, ga, gb);
+      tile_of(min(as_slo, Nt - 1), T, sa, sb);
+      tile_of(min(Lay.Lt + tm_tile(q, as_ja), Nt - 1), T, ta, tb);
     }
     {
       const Step st{vcur, vprev, wv, pcur, cnext, &s_glast, b0, (s + 1) & 31, s + 1, n - 1, v0};
       const int g_lo = as_glo, g_hi = as_ghi;
       float pv = 0.f;
-      if ((wid & 1) == 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
-      mem_tiles<SmemTile>(tsm, Lay.Lg, as_slo, as_shi, T, lane, st, pv);
+      if ((wid & 1) == 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, ga, gb, T, lane, st, pv);
+      mem_tiles<SmemTile>(tsm, Lay.Lg, as_slo, as_shi, sa, sb, T, lane, st, pv);
       if (use_tmem) {
-        tmem_tiles(tq, Lay.Lt, wid & 3, as_ja, as_jb, T, lane, st, pv);
+        tmem_tiles(tq, wid & 3, as_ja, as_jb, ta, tb, T, lane, st, pv);
         tmem_wait_st();
       }
-      if ((wid & 1) != 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, T, lane, st, pv);
+      if ((wid & 1) != 0) mem_tiles<GlobTile>(d.work, 0, g_lo, g_hi, ga, gb, T, lane, st, pv);
       pv = warp_sum(pv);
       if (lane == 0) pvred[wid] = pv;
     }

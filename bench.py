@@ -110,6 +110,23 @@ def _dist():
     return world, rank, local
 
 
+def job_throughput(ms_local, units_local, world):
+    """Whole-job throughput of a weakly scaled run: every rank processes
+    ``units_local`` units (its own shard, no exchange on the data path) in
+    ``ms_local`` ms; the job takes as long as its slowest rank.  Returns
+    (units per second over all ranks, slowest rank's ms).  With world > 1
+    the caller has initialised torch.distributed (NCCL on GPUs, gloo on CPU)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    return world * units_local / (ms / 1000.0), ms
+
+
 def _work_per_candidate(m, rt, k):
     """Algorithmic work of one mixed-form merge evaluation."""
     n = rt + k
@@ -225,7 +242,11 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     import __graft_entry__
-    __graft_entry__.build()
+    # one build per node: the other ranks wait for it, then load the library
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
     from paper_2601_11626_gb300 import csvd, synth
 
     dev = torch.cuda.current_device()
@@ -267,11 +288,7 @@ def main():
         csvd.profile(False)
     ms = e0.elapsed_time(e1)
     barrier()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
-    value = world * n * args.steps / (ms / 1000.0)
+    value, ms = job_throughput(ms, n * args.steps, world)
 
     # dominant kernel roofline
     peaks, peak_src = _peaks()
@@ -382,12 +399,9 @@ def main():
         q1.synchronize()
         qms = q0.elapsed_time(q1) / args.e2e_steps
         h2d_ms = sum(a.elapsed_time(z) for a, z in zip(c0, c1)) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([qms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            qms = float(t)
+        e2e_value, qms = job_throughput(qms, n, world)
         in_bytes = pool.numel() * pool.element_size()
-        e2e = {"value": world * n / (qms / 1000.0), "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                "ms_per_step": qms, "steps": args.e2e_steps,
                "h2d_gbs": in_bytes / (h2d_ms / 1000.0) / 1e9,

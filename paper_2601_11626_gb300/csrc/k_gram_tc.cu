@@ -17,12 +17,13 @@
 //   warp 0      TMA: one 2-D tensor box (32 rows x 128 f32 columns, zero
 //               outside the matrix) per operand into a 5-deep staging ring
 //               (one cp.async.bulk per row when no tensor map is given)
-//   warps 2-9   split staging f32 -> bf16 hi/lo into a 2-deep operand
+//   warps 2-17  split staging f32 -> bf16 hi/lo into a 2-deep operand
 //               ring, K-major with the 64-byte swizzle the UMMA
-//               descriptors expect
-//   warp 1      one thread issues tcgen05.mma (M = N = 128, K = 16) into a
+//               descriptors expect (one 8-deep chunk of one row per thread)
+//   warp 1      one thread issues tcgen05.mma (M = 128, K = 16, N = the
+//               tile's valid columns rounded up to 16) into a
 //               double-buffered f32 accumulator in TMEM and commits
-//   warps 10-13 tcgen05.ld the finished accumulator and store it
+//   warps 18-21 tcgen05.ld the finished accumulator and store it
 // Every mbarrier wait is bounded (2 s of device time); on expiry the CTA
 // sets an abort flag, drains its own copies and MMAs, frees TMEM and
 // reports kStatusWaitCap.
@@ -46,8 +47,10 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 
 // kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, both
 // K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(kTcBN >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kTcBM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -147,11 +150,12 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -276,10 +280,10 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStagesF; ++s) {
       mbar_init(full_st(s), 1);
-      mbar_init(empty_st(s), 8);
+      mbar_init(empty_st(s), kTcConvWarps);
     }
     for (int s = 0; s < kTcStagesB; ++s) {
-      mbar_init(full_bf(s), 8);
+      mbar_init(full_bf(s), kTcConvWarps);
       mbar_init(empty_bf(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -360,6 +364,8 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         if (!mbar_wait(tmem_empty(acc), aph ^ 1u, abort_flag)) break;
         tc_fence_after();
         const uint32_t dt = tmem_base + acc * (uint32_t)kTcBN;
+        // N = the valid columns rounded up to 16: columns past them are not stored
+        const uint32_t idesc = idesc_n(min(kTcBN, (ti.validB + 15) & ~15));
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int slot = it % kTcStagesB;
           const uint32_t ph = (it / kTcStagesB) & 1u;
@@ -374,9 +380,9 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
             const uint32_t o = s * 32;  // 16 bf16 along K
             const uint64_t dah = sw64_desc(ahi + o), dal = sw64_desc(alo + o);
             const uint64_t dbh = sw64_desc(bhi + o), dbl = sw64_desc(blo + o);
-            umma(dt, dah, dbh, (kb | s) != 0 ? 1u : 0u);
-            umma(dt, dah, dbl, 1u);
-            umma(dt, dal, dbh, 1u);
+            umma(dt, dah, dbh, idesc, (kb | s) != 0 ? 1u : 0u);
+            umma(dt, dah, dbl, idesc, 1u);
+            umma(dt, dal, dbh, idesc, 1u);
           }
           umma_commit(empty_bf(slot));
         }
@@ -388,11 +394,14 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       mbar_wait(final_bar, 0, abort_flag, false);
     }
     __syncwarp();
-  } else if (warp < 10) {
+  } else if (warp < 2 + kTcConvWarps) {
     // ---------------------------------------------------- converters
-    const int tc = threadIdx.x - 64;  // 0..255
+    // Thread -> (row, 8-deep chunk).  Rows past an operand's valid extent
+    // are not split: they only feed output rows / columns that are never
+    // stored (each output element depends on one row of each operand).
+    const int tc = threadIdx.x - 64;  // 0 .. 32 kTcConvWarps - 1
     const int row = tc & 127;
-    const int c0 = (tc >> 7) * 2;
+    const int c = tc >> 7;
     uint32_t it = 0;
     bool ok = true;
     for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
@@ -407,44 +416,33 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         uint8_t* op = smem + kOpBase + bs * kTcStageB;
         const float* sa = reinterpret_cast<const float*>(st + kStA);
         const float* sb = reinterpret_cast<const float*>(st + kStB);
+        const uint32_t off = sw64_off(row, c);
+        const bool do_a = row < ti.validA, do_b = !ti.diag && row < ti.validB;
+        float x[8];
         if (masked) {
-          // per-row copies leave rows past m and columns past k unwritten
+          // per-row copies leave rows past m unwritten: zero the K tail
           const int lmax = ti.m - kb * kTcBK;
+          if (do_a) {
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int c = c0 + cc;
-            const uint32_t off = sw64_off(row, c);
-            float x[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int l = c * 8 + e;
-              x[e] = (l < lmax && row < ti.validA) ? sa[l * kTcBM + row] : 0.f;
-            }
+            for (int e = 0; e < 8; ++e) x[e] = (c * 8 + e < lmax) ? sa[(c * 8 + e) * kTcBM + row] : 0.f;
             split_store(op + kAhi, op + kAlo, off, x);
-            if (!ti.diag) {
+          }
+          if (do_b) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int l = c * 8 + e;
-                x[e] = (l < lmax && row < ti.validB) ? sb[l * kTcBN + row] : 0.f;
-              }
-              split_store(op + kBhi, op + kBlo, off, x);
-            }
+            for (int e = 0; e < 8; ++e) x[e] = (c * 8 + e < lmax) ? sb[(c * 8 + e) * kTcBN + row] : 0.f;
+            split_store(op + kBhi, op + kBlo, off, x);
           }
         } else {
           // tensor boxes arrive zero-filled outside the matrix
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int c = c0 + cc;
-            const uint32_t off = sw64_off(row, c);
-            float x[8];
+          if (do_a) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) x[e] = sa[(c * 8 + e) * kTcBM + row];
             split_store(op + kAhi, op + kAlo, off, x);
-            if (!ti.diag) {
+          }
+          if (do_b) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) x[e] = sb[(c * 8 + e) * kTcBN + row];
-              split_store(op + kBhi, op + kBlo, off, x);
-            }
+            for (int e = 0; e < 8; ++e) x[e] = sb[(c * 8 + e) * kTcBN + row];
+            split_store(op + kBhi, op + kBlo, off, x);
           }
         }
         fence_async_smem();

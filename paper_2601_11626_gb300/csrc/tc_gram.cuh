@@ -30,7 +30,8 @@ struct TcTile {
 // latency) and split bf16 operand slots read by the MMAs.
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32;
 constexpr int kTcStagesF = 5, kTcStagesB = 2;
-constexpr int kTcThreads = 14 * 32;
+constexpr int kTcConvWarps = 16;  // split warps: one 8-deep chunk of one row each
+constexpr int kTcThreads = (2 + kTcConvWarps + 4) * 32;
 constexpr int kTcStageF = 2 * kTcBK * kTcBM * 4;  // 32 KB: A and B rows, f32
 constexpr int kTcStageB = 4 * kTcBM * kTcBK * 2;  // 32 KB: A hi/lo, B hi/lo, bf16
 constexpr int kTcSmemBytes = kTcStagesF * kTcStageF + kTcStagesB * kTcStageB + 2048;

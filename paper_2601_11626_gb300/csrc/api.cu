@@ -274,25 +274,27 @@ int device_sm_count() { return num_sms(); }
 csvd_status set_error(csvd_status st, const char* msg);
 }  // namespace csvd
 
+// SM count of the current device (cached per device).
 static int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 148;
+      n = 152;
+    cache[dev].store(n, std::memory_order_relaxed);
   }
   return n;
 }
 
 // The Gram of the mixed form runs on the tensor cores unless CSVD_GRAM=simt.
 static bool gram_on_tensor_cores() {
-  static int mode = -1;
-  if (mode < 0) {
+  static const bool on = [] {
     const char* e = std::getenv("CSVD_GRAM");
-    mode = (e && std::strcmp(e, "simt") == 0) ? 0 : 1;
-  }
-  return mode == 1;
+    return !(e && std::strcmp(e, "simt") == 0);
+  }();
+  return on;
 }
 
 // ------------------------------------------------------- TMA tensor maps
@@ -320,16 +322,15 @@ static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_maps;
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+  });
   return fn;
 }
 

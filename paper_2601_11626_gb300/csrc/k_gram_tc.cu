@@ -509,13 +509,10 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
 cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles, int n_ctas,
                            int* d_status, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // per device and cheap: set on every launch
+  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kTcSmemBytes);
+  if (e != cudaSuccess) return e;
   if (n_ctas > n_tiles) n_ctas = n_tiles;
   prof_begin(s);
   tc_gram_kernel<<<n_ctas, kTcThreads, kTcSmemBytes, s>>>(d_items, d_tiles, n_tiles, d_status);

@@ -178,6 +178,25 @@ csvd_status csvd_gram_apply(const float* U, int64_t ldu, int64_t m, int32_t r,
                             const csvd_block* blocks, int32_t n, float* Y, int64_t ldy,
                             void* cuda_stream);
 
+/* Final decomposition of one cluster (Section 2, problem formulation): with
+ * the cluster's rank-r left basis U (m x r, orthonormal columns, row-major,
+ * device, ldu) and singular values s (r floats, device) the cluster keeps
+ * U~ = U diag(s) and, per block A_i (m x k_i), the coefficient block
+ * V_i = A_i^T U diag(s)^-1 (k_i x r; columns with s_j = 0 are zero), so that
+ * A^_i = U~ V_i^T = U U^T A_i.  With U, s the exact top-r SVD of the
+ * concatenation, the stacked V has orthonormal columns.  Writes U~ to Ut_out
+ * (m x r, row-major, device, ldut >= r; may be NULL), V_i to V_out[i]
+ * (device pointers, row-major with leading dimension ldv >= r; V_out may be
+ * NULL) and, on the host, resid_sq[i] = ||A_i - A^_i||_F^2 from the
+ * explicit residual and energy[i] = ||A_i||_F^2 (FP64); the cluster's
+ * relative reconstruction error (Section 4) is
+ * sqrt(sum resid_sq / sum energy) and its storage r (m + sum k_i) numbers.
+ * Blocks are f32.  Syncs. */
+csvd_status csvd_reconstruct(const float* U, int64_t ldu, const float* s, int64_t m, int32_t r,
+                             const csvd_block* blocks, int32_t n, float* Ut_out, int64_t ldut,
+                             float* const* V_out, int64_t ldv, void* cuda_stream,
+                             double* resid_sq, double* energy);
+
 /* ||A_j||_F^2 of each block (Kahan-compensated FP32 partial sums, FP64
  * totals) into energy_host[0..n).  Syncs. */
 csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m, void* cuda_stream,

@@ -1649,6 +1649,80 @@ extern "C" csvd_status csvd_tail_grad(const float* U, int64_t ldu, int64_t m, in
   return CSVD_OK;
 }
 
+// Final decomposition of a cluster (Section 2): V_i = A_i^T U diag(s)^-1 and
+// the explicit residuals A_i - U U^T A_i with their energies.
+extern "C" csvd_status csvd_reconstruct(const float* U, int64_t ldu, const float* s, int64_t m,
+                                        int32_t r, const csvd_block* blocks, int32_t n,
+                                        float* Ut_out, int64_t ldut, float* const* V_out,
+                                        int64_t ldv, void* cuda_stream, double* resid_sq,
+                                        double* energy) {
+  if (!U || !s || !blocks || n < 0 || m < 1 || r < 1 || ldu < r || !resid_sq || !energy)
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  if (V_out && ldv < r) return fail(CSVD_ERR_ARG, "ldv < r");
+  if (Ut_out && ldut < r) return fail(CSVD_ERR_ARG, "ldut < r");
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_ARG, "decomposition takes f32 blocks");
+    if (V_out && !V_out[i]) return fail(CSVD_ERR_ARG, "NULL V_out entry");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (Ut_out) CUDA_TRY(launch_scale_cols(U, ldu, (int)m, r, s, 0, Ut_out, ldut, st));
+  if (n == 0) return CSVD_OK;
+  // workspace: U diag(s)^-1, and per block P = U^T A (r x k) and R = A - U P (m x k)
+  Layout L;
+  const size_t oUs = L.add(sizeof(float) * (size_t)m * r);
+  std::vector<size_t> oP(n), oR(n);
+  for (int i = 0; i < n; ++i) {
+    oP[i] = L.add(sizeof(float) * (size_t)r * blocks[i].k);
+    oR[i] = L.add(sizeof(float) * (size_t)m * blocks[i].k);
+  }
+  GemmBatch gP, gR, gV;
+  auto fill = [&](char* base) {
+    gP = GemmBatch(); gR = GemmBatch(); gV = GemmBatch();
+    const float* Us = reinterpret_cast<const float*>(base + oUs);
+    for (int i = 0; i < n; ++i) {
+      const int k = (int)blocks[i].k;
+      float* P = reinterpret_cast<float*>(base + oP[i]);
+      float* R = reinterpret_cast<float*>(base + oR[i]);
+      gP.add(gemm(U, ldu, 1, blocks[i].ptr, blocks[i].ld, 0, P, k, 0, r, k, (int)m));
+      gR.add(gemm(U, ldu, 0, P, k, 0, R, k, 0, (int)m, k, r, -1.f,
+                  reinterpret_cast<const float*>(blocks[i].ptr), blocks[i].ld, 0, 1.f));
+      // V_i = (Us^T A_i)^T, written transposed (k x r)
+      if (V_out) gV.add(gemm(Us, r, 1, blocks[i].ptr, blocks[i].ld, 0, V_out[i], ldv, 1, r, k, (int)m));
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  gP.pack(probe); gR.pack(probe); gV.pack(probe);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = st;
+  w.base = static_cast<char*>(dev_alloc(L.size, st));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  gP.pack(pk); gR.pack(pk); gV.pack(pk);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), st));
+  if (V_out) CUDA_TRY(launch_scale_cols(U, ldu, (int)m, r, s, 1, w.at<float>(oUs), r, st));
+  CUDA_TRY(gP.launch(dbase, st));
+  CUDA_TRY(gR.launch(dbase, st));
+  if (V_out) CUDA_TRY(gV.launch(dbase, st));
+  // energies of the residuals and of the blocks
+  std::vector<csvd_block> rb(n);
+  for (int i = 0; i < n; ++i) rb[i] = csvd_block{w.base + oR[i], blocks[i].k, blocks[i].k, CSVD_F32, 0};
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::vector<double> er, ea;
+  CSVD_TRY(block_energies(rb.data(), idx, m, st, er));
+  CSVD_TRY(block_energies(blocks, idx, m, st, ea));
+  for (int i = 0; i < n; ++i) {
+    resid_sq[i] = er[i];
+    energy[i] = ea[i];
+  }
+  return CSVD_OK;
+}
+
 extern "C" csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m,
                                          void* cuda_stream, double* energy_host) {
   if (!blocks || n < 0 || m < 1 || !energy_host) return fail(CSVD_ERR_ARG, "bad arguments");

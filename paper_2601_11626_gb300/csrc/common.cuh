@@ -172,5 +172,7 @@ cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
                                 double* scal, cudaStream_t s);
 cudaError_t launch_add_inplace(float* dst, const float* src, int rows, int cols,
                                int64_t ld_dst, int64_t ld_src, cudaStream_t s);
+cudaError_t launch_scale_cols(const float* U, int64_t ldu, int m, int r, const float* s,
+                              int inverse, float* out, int64_t ld_out, cudaStream_t st);
 
 }  // namespace csvd

@@ -292,4 +292,30 @@ cudaError_t launch_add_inplace(float* dst, const float* src, int rows, int cols,
   return cudaGetLastError();
 }
 
+// Column scaling of an m x r row-major factor: out[i][j] = U[i][j] * s[j]
+// (U~ = U diag(s)), or with `inverse` U[i][j] / s[j] (0 where s[j] == 0).
+__global__ void scale_cols_kernel(const float* __restrict__ U, int64_t ldu, int m, int r,
+                                  const float* __restrict__ s, int inverse,
+                                  float* __restrict__ out, int64_t ld_out) {
+  const int64_t total = (int64_t)m * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    const float sj = s[j], u = U[(int64_t)i * ldu + j];
+    out[(int64_t)i * ld_out + j] = inverse ? (sj > 0.f ? u / sj : 0.f) : u * sj;
+  }
+}
+
+cudaError_t launch_scale_cols(const float* U, int64_t ldu, int m, int r, const float* s,
+                              int inverse, float* out, int64_t ld_out, cudaStream_t st) {
+  const int64_t total = (int64_t)m * r;
+  if (total <= 0) return cudaSuccess;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  prof_begin(st);
+  scale_cols_kernel<<<blocks, 256, 0, st>>>(U, ldu, m, r, s, inverse, out, ld_out);
+  prof_end("scale_cols", st);
+  return cudaGetLastError();
+}
+
 }  // namespace csvd

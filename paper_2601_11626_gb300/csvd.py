@@ -8,6 +8,7 @@ is missing or no GPU is present.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import enum
 import os
 
@@ -56,6 +57,8 @@ def _sig(lib):
     lib.csvd_incr_sigma.argtypes = [VP, P(C.c_float), P(I32)]
     lib.csvd_incr_load.argtypes = [VP, VP, I64, I32, P(C.c_float), D, D]
     lib.csvd_gram_apply.argtypes = [VP, I64, I64, I32, P(Block), I32, VP, I64, VP]
+    lib.csvd_reconstruct.argtypes = [VP, I64, VP, I64, I32, P(Block), I32, VP, I64, VP, I64, VP,
+                                     P(D), P(D)]
     lib.csvd_incr_basis.argtypes = [VP, VP, I64]
     lib.csvd_tail_error.argtypes = [VP, P(D), P(D), P(D), P(D)]
     lib.csvd_incr_free.argtypes = [VP]
@@ -167,6 +170,13 @@ class IncrSVD:
         reff = C.c_int32()
         _check(self._lib.csvd_incr_sigma(self._h, None, C.byref(reff)))
         return reff.value
+
+    def decompose(self, blocks, want_v: bool = True) -> "Decomposition":
+        """Final decomposition of the cluster whose blocks were appended:
+        U~ = U diag(sigma~) and V_i = A_i^T U diag(sigma~)^-1 from this state."""
+        U = self.basis()
+        sig = self.sigma()[: U.shape[1]]
+        return reconstruct(U, sig, blocks, want_v)
 
     def basis(self) -> torch.Tensor:
         rk = self.rank
@@ -314,6 +324,46 @@ def tail_grad(U: torch.Tensor, blocks, g: float = 1.0):
                                 _blocks(blocks), _blocks(grads), len(blocks), float(g),
                                 _stream()))
     return grads
+
+
+class Decomposition:
+    """Final decomposition of one cluster: U~ = U diag(s) and the coefficient
+    blocks V_i (k_i x r), so that A^_i = U~ V_i^T; per-block residual and
+    block energies (FP64) and the cluster's relative reconstruction error."""
+
+    def __init__(self, Ut, V, resid_sq, energy):
+        self.Ut, self.V = Ut, V
+        self.resid_sq, self.energy = resid_sq, energy
+
+    @property
+    def rel_error(self) -> float:
+        tot = float(self.energy.sum())
+        return math.sqrt(float(self.resid_sq.sum()) / tot) if tot > 0 else 0.0
+
+    @property
+    def memory(self) -> int:
+        """Stored numbers r (m + N_c)."""
+        return self.Ut.shape[0] * self.Ut.shape[1] + sum(v.shape[0] * v.shape[1] for v in self.V)
+
+
+def reconstruct(U: torch.Tensor, s, blocks, want_v: bool = True) -> Decomposition:
+    """Decomposition of a cluster from its basis U (m x r) and singular
+    values s (r): V_i = A_i^T U diag(s)^-1, residual energies from the
+    explicit residuals A_i - U U^T A_i."""
+    m, r = U.shape
+    U = U.contiguous().float()
+    sd = torch.as_tensor(np.asarray(s, dtype=np.float32), device="cuda").contiguous()
+    n = len(blocks)
+    V = [torch.empty(b.shape[1], r, device="cuda", dtype=torch.float32) for b in blocks] if want_v else []
+    vptr = (C.c_void_p * n)(*[v.data_ptr() for v in V]) if want_v else None
+    Ut = torch.empty(m, r, device="cuda", dtype=torch.float32)
+    res = (C.c_double * max(n, 1))()
+    en = (C.c_double * max(n, 1))()
+    _check(lib().csvd_reconstruct(C.c_void_p(U.data_ptr()), U.stride(0), C.c_void_p(sd.data_ptr()), m,
+                                  r, _blocks(blocks), n, C.c_void_p(Ut.data_ptr()), r, vptr, r,
+                                  _stream(), res, en))
+    return Decomposition(Ut, V, np.array(res[:n], dtype=np.float64),
+                         np.array(en[:n], dtype=np.float64))
 
 
 def gram_apply(U: torch.Tensor, blocks) -> torch.Tensor:

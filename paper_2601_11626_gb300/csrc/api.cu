@@ -386,9 +386,87 @@ struct CommitKeep {  // workspace kept for the commit of a single plain item
   int kp = 0, nr = 0, r_new = 0;
 };
 
+// Mixed-form evaluations of one-column candidates: the Gram of the core is
+// an arrowhead, solved by bisection on its exact O(r_t) inertia count.
+static bool arrow_eligible(const Item& it) {
+  return it.blk->k == 1 && it.blk->dtype == CSVD_F32 && it.st.rt <= kArrowMaxRt;
+}
+
+static_assert(sizeof(ArrowDesc) % alignof(int2) == 0, "group table follows the descriptors");
+
+static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, cudaStream_t s,
+                                   int* d_status) {
+  const int n = (int)items.size();
+  if (n == 0) return CSVD_OK;
+  // candidates of one state side by side, in groups of up to kArrowGroup
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return reinterpret_cast<uintptr_t>(items[x].st.U) < reinterpret_cast<uintptr_t>(items[y].st.U);
+  });
+  std::vector<int2> groups;
+  for (int i = 0; i < n; ++i) {
+    if (groups.empty() || groups.back().y == kArrowGroup ||
+        items[order[i]].st.U != items[order[groups.back().x]].st.U)
+      groups.push_back(make_int2(i, 0));
+    ++groups.back().y;
+  }
+  std::vector<ArrowDesc> ad(n);
+  for (int i = 0; i < n; ++i) {
+    const Item& it = items[order[i]];
+    ArrowDesc& d = ad[i];
+    d.a = reinterpret_cast<const float*>(it.blk->ptr);
+    d.lda = it.blk->ld;
+    d.U = it.st.U;
+    d.ldu = it.st.ldu;
+    d.m = it.m;
+    d.rt = it.st.rt;
+    d.r_new = std::min<int64_t>(it.r, it.st.rt + std::min<int64_t>(1, it.m - it.st.rt));
+    d.sigma = it.st.sigma;
+    d.scal = it.st.scal;
+    d.sigma_out = it.sigma_out;
+    d.tail_out = it.tail_out;
+    d.tail_paper_out = it.tail_paper_out;
+    d.energy_out = it.energy_out;
+    d.accept_out = it.accept_out;
+    d.eps = eps;
+  }
+  const size_t desc_bytes = sizeof(ArrowDesc) * n, group_bytes = sizeof(int2) * groups.size();
+  std::vector<char> host(desc_bytes + group_bytes);
+  std::memcpy(host.data(), ad.data(), desc_bytes);
+  std::memcpy(host.data() + desc_bytes, groups.data(), group_bytes);
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(host.size(), s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  CUDA_TRY(upload(w.base, host.data(), host.size(), s));
+  CUDA_TRY(launch_core_arrow(w.at<ArrowDesc>(0), w.at<int2>(desc_bytes), (int)groups.size(),
+                             d_status, s));
+  return CSVD_OK;
+}
+
+static csvd_status run_items_general(const std::vector<Item>& items, double eps, int precision,
+                                     cudaStream_t s, int* d_status, Workspace& ws,
+                                     CommitKeep* keep, bool want_W);
+
 static csvd_status run_items(const std::vector<Item>& items, double eps, int precision,
                              cudaStream_t s, int* d_status, Workspace& ws, CommitKeep* keep,
                              bool want_W) {
+  if (precision == CSVD_MIXED && !want_W) {
+    std::vector<Item> arrow, rest;
+    for (const Item& it : items) (arrow_eligible(it) ? arrow : rest).push_back(it);
+    if (!arrow.empty()) {
+      CSVD_TRY(run_arrow_items(arrow, eps, s, d_status));
+      return rest.empty() ? CSVD_OK : run_items_general(rest, eps, precision, s, d_status, ws, keep,
+                                                        want_W);
+    }
+  }
+  return run_items_general(items, eps, precision, s, d_status, ws, keep, want_W);
+}
+
+static csvd_status run_items_general(const std::vector<Item>& items, double eps, int precision,
+                                     cudaStream_t s, int* d_status, Workspace& ws,
+                                     CommitKeep* keep, bool want_W) {
   const int n = (int)items.size();
   if (n == 0) return CSVD_OK;
   Layout L;

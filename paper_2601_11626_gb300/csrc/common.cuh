@@ -92,6 +92,30 @@ struct CoreDesc {
   int in_smem, pad;
 };
 
+// ----------------------------------------------------- one-column merges
+// Mixed-form evaluation of a one-column candidate a (m values, stride lda)
+// against a state (U: m x rt, ldu; sigma; scal = {energy, discarded}).
+// Candidates of one state are launched in groups of up to kArrowGroup
+// (int2 {first descriptor, count} per CTA) so that U is read once per group.
+constexpr int kArrowMaxRt = 128;
+constexpr int kArrowGroup = 4;
+struct ArrowDesc {
+  const float* a;
+  int64_t lda;
+  const float* U;
+  int64_t ldu;
+  int64_t m;
+  int rt, r_new;
+  const float* sigma;
+  const double* scal;
+  float* sigma_out;
+  double* tail_out;
+  double* tail_paper_out;  // may be null
+  double* energy_out;      // may be null
+  uint8_t* accept_out;     // may be null
+  double eps;
+};
+
 // ------------------------------------------------------------ energy
 struct EnergyDesc {
   const void* A;
@@ -166,6 +190,8 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
                                int* d_status, cudaStream_t s);
 cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
                                 int* d_status, cudaStream_t s);
+cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
+                              int* d_status, cudaStream_t s);
 cudaError_t launch_gram_dev(const float* U, int64_t ldu, int m, int r, float* D, cudaStream_t s);
 cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
                                 const double* energy_new, const double* tail_new,

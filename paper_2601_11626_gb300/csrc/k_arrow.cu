@@ -1,0 +1,250 @@
+// One-column merge evaluations (k = 1) in the mixed form.
+//
+// With a single new column a, the Gram of the core (Lemma 1) is an arrowhead
+//     G = [[diag(d), z], [z^T, alpha]],  d_j = s_j^2, z_j = s_j p_j,
+//     p = U^T a, alpha = ||a||^2   (n = r_t + 1),
+// whose eigenvalues are the squared singular values of the merge.  For x off
+// the poles d_j, G - xI has as many negative eigenvalues as diag(d) - xI
+// plus the sign of its Schur complement, so
+//     #{lambda < x} = #{j : d_j < x} + [alpha - x - sum_j z_j^2 / (d_j - x) < 0],
+// an exact O(r_t) count.  Multisection bisection on it gives the top r_new
+// eigenvalues (sigma~_j = sqrt(lambda_j), Cor. 3) and the tail follows from
+// the trace, tr(G) - sum of the top, in FP64.  diag(d) is the leading
+// principal block of G, so (Cauchy interlacing) with s non-increasing the
+// q-th largest eigenvalue lies in [d_q, d_{q-1}]: that bracket, not the whole
+// Gershgorin interval, starts its bisection.
+//
+// One 128-thread CTA per group of up to kArrowGroup candidates of the same
+// state: rows of the group's columns are staged in shared memory 128 at a
+// time and every row of U read from L2 serves the whole group.
+#include "common.cuh"
+
+namespace csvd {
+namespace {
+
+constexpr int kArrowThreads = 128;
+constexpr int kArrowWarps = kArrowThreads / 32;
+constexpr int kArrowBisectMax = 64;
+static_assert(kArrowGroup == 4, "rows of the group are staged as float4");
+static_assert(kArrowGroup <= kArrowWarps, "one warp per candidate in the per-item steps");
+
+__device__ __forceinline__ int arrow_count(const float* d, const float* z2, int rt, float alpha,
+                                           float x, float pivmin) {
+  int c = 0;
+  float s = alpha - x;
+  for (int j = 0; j < rt; ++j) {
+    float q = d[j] - x;
+    c += q < 0.f;
+    if (fabsf(q) < pivmin) q = q < 0.f ? -pivmin : pivmin;
+    s -= __fdividef(z2[j], q);
+  }
+  return c + (s < 0.f);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kArrowThreads)
+core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ groups,
+                  int* __restrict__ status) {
+  const int2 gr = groups[blockIdx.x];
+  const ArrowDesc* D = descs + gr.x;
+  const int cnt = gr.y;
+  const int rt = D[0].rt, n = rt + 1, rq = D[0].r_new;
+  const int64_t m = D[0].m, ldu = D[0].ldu;
+  const float* __restrict__ U = D[0].U;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  __shared__ float4 s_a[kArrowThreads];
+  __shared__ float s_part[kArrowWarps][kArrowGroup][32];
+  __shared__ float s_d[kArrowMaxRt];
+  __shared__ float s_z2[kArrowGroup][kArrowMaxRt];
+  __shared__ float s_lam[kArrowGroup][kArrowMaxRt + 1];
+  __shared__ float s_lo[kArrowGroup], s_hi[kArrowGroup];
+  __shared__ double s_red[kArrowWarps][kArrowGroup];
+  __shared__ double s_alpha[kArrowGroup];
+
+  const float* ap[kArrowGroup];
+  int64_t lda[kArrowGroup];
+#pragma unroll
+  for (int g = 0; g < kArrowGroup; ++g) {
+    ap[g] = g < cnt ? D[g].a : nullptr;
+    lda[g] = g < cnt ? D[g].lda : 0;
+  }
+
+  // 1. p = U^T a for every candidate and ||a||^2 (FP64 totals).  The r_t
+  //    columns of U are cut into 32-wide slabs, one per warp; warps left
+  //    over split the rows of each staged chunk between them.
+  const int nslab = (rt + 31) / 32;
+  const int nrg = nslab > 0 ? kArrowWarps / nslab : 1;
+  const int slab = nslab > 0 ? wid % nslab : 0, rg = nslab > 0 ? wid / nslab : wid;
+  const int col = slab * 32 + lane;
+  const bool pj_on = nslab > 0 && rg < nrg && col < rt;
+  float acc[kArrowGroup] = {};
+  double aa[kArrowGroup] = {};
+  for (int64_t i0 = 0; i0 < m; i0 += kArrowThreads) {
+    const int64_t i = i0 + tid;
+    float v[kArrowGroup];
+#pragma unroll
+    for (int g = 0; g < kArrowGroup; ++g) {
+      v[g] = (g < cnt && i < m) ? ap[g][i * lda[g]] : 0.f;
+      aa[g] = fma((double)v[g], (double)v[g], aa[g]);
+    }
+    s_a[tid] = make_float4(v[0], v[1], v[2], v[3]);
+    __syncthreads();
+    if (pj_on) {
+      const int len = (int)(m - i0 < kArrowThreads ? m - i0 : kArrowThreads);
+      const float* u = U + i0 * ldu + col;
+#pragma unroll 8
+      for (int ii = rg; ii < len; ii += nrg) {
+        const float uu = __ldg(u + (int64_t)ii * ldu);
+        const float4 x = s_a[ii];
+        acc[0] = fmaf(uu, x.x, acc[0]);
+        acc[1] = fmaf(uu, x.y, acc[1]);
+        acc[2] = fmaf(uu, x.z, acc[2]);
+        acc[3] = fmaf(uu, x.w, acc[3]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int g = 0; g < kArrowGroup; ++g) {
+    s_part[wid][g][lane] = acc[g];
+    const double t = warp_sum_d(aa[g]);
+    if (lane == 0) s_red[wid][g] = t;
+  }
+  __syncthreads();
+  if (tid < kArrowGroup) {
+    double t = 0.0;
+    for (int w = 0; w < kArrowWarps; ++w) t += s_red[w][tid];
+    s_alpha[tid] = t;
+  }
+  bool sorted_ok = true;
+  if (tid < rt) {
+    const int sl = tid / 32, ln = tid % 32;
+    const float sj = D[0].sigma[tid];
+    s_d[tid] = sj * sj;
+    if (tid + 1 < rt) sorted_ok = sj >= D[0].sigma[tid + 1];
+#pragma unroll
+    for (int g = 0; g < kArrowGroup; ++g) {
+      float p = 0.f;
+      for (int r2 = 0; r2 < nrg; ++r2) p += s_part[r2 * nslab + sl][g][ln];
+      const float zj = sj * p;
+      s_z2[g][tid] = zj * zj;
+    }
+  }
+  const bool sorted = __syncthreads_and(sorted_ok);
+
+  // 2. Gershgorin interval of each arrowhead (warp g <-> candidate g)
+  if (wid < cnt) {
+    const float alpha = (float)s_alpha[wid];
+    float lo = alpha, hi = alpha, zsum = 0.f;
+    for (int j = lane; j < rt; j += 32) {
+      const float zj = sqrtf(s_z2[wid][j]);
+      lo = fminf(lo, s_d[j] - zj);
+      hi = fmaxf(hi, s_d[j] + zj);
+      zsum += zj;
+    }
+    zsum = warp_sum(zsum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      s_lo[wid] = fminf(lo, alpha - zsum);
+      s_hi[wid] = fmaxf(hi, alpha + zsum);
+    }
+  }
+  __syncthreads();
+
+  // 3. multisection bisection: one task per (candidate, eigenvalue), g
+  //    threads per task
+  const int ntask = cnt * rq;
+  int g = 1;
+  while (g < 16 && g * 2 * ntask <= kArrowThreads) g *= 2;
+  const int ngroups = kArrowThreads / g;
+  const int grp = tid / g, sub = tid % g;
+  const unsigned shift = (unsigned)((lane / g) * g);
+  const unsigned gmask = ((1u << g) - 1u) << shift;
+  int capped = 0;
+  for (int t0 = 0; t0 < ntask; t0 += ngroups) {  // uniform trip count across the block
+    const int t = t0 + grp;
+    const bool active = t < ntask;
+    const int item = active ? t / rq : 0, q = active ? t % rq : 0;
+    const int target = n - 1 - q;  // ascending index of the q-th largest
+    const float glo = s_lo[item], ghi = s_hi[item];
+    const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
+    const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
+    const float atol = 2.4e-7f * gnorm + 1e-30f;
+    const float alpha = (float)s_alpha[item];
+    const float* z2 = s_z2[item];
+    float a = glo, b = ghi;
+    if (sorted) {
+      if (q > 0) b = fminf(b, s_d[q - 1]);
+      if (q < rt) a = fmaxf(a, s_d[q]);
+      if (a > b) a = b;
+    }
+    bool stuck = false;
+    int it = 0;
+    for (; it < kArrowBisectMax; ++it) {
+      const bool done = !active || stuck || !((b - a) > atol);
+      if (__all_sync(0xffffffffu, done)) break;
+      const float step = (b - a) / (float)(g + 1);
+      const float x = a + step * (float)(sub + 1);
+      bool above = false;
+      if (!done)
+        above = (x > a && x < b) ? (arrow_count(s_d, z2, rt, alpha, x, pivmin) > target)
+                                 : (x >= b);
+      const unsigned bal = (__ballot_sync(0xffffffffu, above) & gmask) >> shift;
+      if (!done) {
+        const int s = bal ? __ffs(bal) - 1 : g;
+        const float na = (s == 0) ? a : a + step * (float)s;
+        const float nb = (s == g) ? b : a + step * (float)(s + 1);
+        if (!(nb < b || na > a)) stuck = true;
+        a = na;
+        b = nb;
+      }
+    }
+    if (active && it == kArrowBisectMax) capped = 1;
+    if (active && sub == 0) s_lam[item][q] = 0.5f * (a + b);
+  }
+  if (capped) atomicOr(status, kStatusBisectCap);
+  __syncthreads();
+
+  // 4. FP64 epilogue (warp g <-> candidate g): sigma~, tail from the trace,
+  //    energy, accept flag
+  if (wid < cnt) {
+    const ArrowDesc& dsc = D[wid];
+    const double alpha_d = s_alpha[wid];
+    double top = 0.0, tr = 0.0;
+    for (int q = lane; q < rq; q += 32) {
+      top += (double)s_lam[wid][q];
+      dsc.sigma_out[q] = sqrtf(fmaxf(s_lam[wid][q], 0.f));
+    }
+    for (int j = lane; j < rt; j += 32) tr += (double)s_d[j];
+    top = warp_sum_d(top);
+    tr = warp_sum_d(tr) + alpha_d;
+    if (lane == 0) {
+      const double energy_new = dsc.scal[0] + alpha_d;
+      double tail = dsc.scal[1] + (tr - top);
+      if (tail < 0.0) tail = 0.0;
+      double paper = energy_new - top;
+      if (paper < 0.0) paper = 0.0;
+      dsc.tail_out[0] = tail;
+      if (dsc.tail_paper_out) dsc.tail_paper_out[0] = paper;
+      if (dsc.energy_out) dsc.energy_out[0] = energy_new;
+      if (dsc.accept_out) dsc.accept_out[0] = (tail <= dsc.eps * dsc.eps * energy_new) ? 1 : 0;
+    }
+  }
+}
+
+cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
+                              int* d_status, cudaStream_t s) {
+  if (n_groups <= 0) return cudaSuccess;
+  prof_begin(s);
+  core_arrow_kernel<<<n_groups, kArrowThreads, 0, s>>>(d_desc, d_groups, d_status);
+  prof_end("core_arrow", s);
+  return cudaGetLastError();
+}
+
+}  // namespace csvd

@@ -93,14 +93,16 @@ def _oracle_states(m, r, groups):
 
 
 # ------------------------------------------------- one merge evaluation
-def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision):
+def _compare_scores(csvd, gst, cst, cand_state, cands, eps, precision, tail_floor=0.0):
+    """``tail_floor``: absolute tail error allowed as a fraction of the merged
+    energy ||M||^2 (the mixed form's cancellation floor, for tails near 0)."""
     sig, tail, paper, acc = csvd.score(gst, cand_state, cands, eps, precision)
     sig, tail, paper, acc = _np(sig), _np(tail), _np(paper), acc.cpu().numpy()
     boundary = []
     for i, (si, b) in enumerate(zip(cand_state, cands)):
         s_o, t_o, a_o, nxt = cst[si].evaluate(b.cpu(), eps)
         _check_sigma(sig[i, :len(s_o)], s_o, mixed=(precision == "mixed"))
-        _check_tail(tail[i], nxt[3])
+        _check_tail(tail[i], nxt[3], floor=math.sqrt(tail_floor * nxt[2]))
         rel = math.sqrt(t_o / nxt[2])
         if abs(rel - eps) <= 1e-3 * eps:
             boundary.append(i)
@@ -159,6 +161,54 @@ def test_score_eigen_core_layout_boundaries(csvd):
     # mix in latent-subspace blocks so that some merges are accepted
     blocks = list(blocks) + list(w["candidates"])
     _compare_scores(csvd, gst, cst, [0] * len(blocks), blocks, 0.25, "mixed")
+
+
+def test_score_one_column_arrowhead(csvd):
+    """One-column candidates in the mixed form (the arrowhead core) against the
+    oracle: a fresh state (r_t = 0), truncating states with r_t = 24 and
+    r_t = 128 (the largest arrowhead), r_t = 160 (past it, the general core),
+    and a state that fills every row (no new direction, k' = 0).  Columns are
+    random, inside the span of U (plus a little noise), zero, and strided
+    views of a wider matrix; two-column candidates ride in the same batch."""
+    m = 768
+    specs = [(32, []), (24, [16, 24]), (128, [96, 64]), (160, [120, 80])]
+    cst, gst = [], []
+    for r, widths in specs:
+        raw = [b.cpu() for b in synth.random_blocks(m, widths, seed=r, decay=0.97)] if widths else []
+        cst += _oracle_states(m, r, [raw])
+        gst.append(_load(csvd, cst[-1]))
+    assert [int(g.rank) for g in gst] == [0, 24, 128, 160]
+    gen = torch.Generator().manual_seed(5)
+    cands, cand_state = [], []
+    scales = [math.sqrt(max(c.energy, 1.0) / m) for c in cst]
+    wide = torch.randn(m, 9, generator=gen, dtype=torch.float64)
+    wide = (wide * torch.tensor(scales + [1.0] * (9 - len(scales)))).float().cuda()
+    for si, c in enumerate(cst):
+        Q = torch.tensor(c.Q, dtype=torch.float64)
+        scale = scales[si]
+        cols = [torch.randn(m, 1, generator=gen, dtype=torch.float64) * scale]
+        if c.Q.shape[1] > 0:
+            w = torch.randn(c.Q.shape[1], 1, generator=gen, dtype=torch.float64)
+            inspan = Q @ (w * torch.tensor(c.s[:, None]))
+            cols.append(inspan + 1e-3 * scale * torch.randn(m, 1, generator=gen, dtype=torch.float64))
+            cols.append(torch.zeros(m, 1, dtype=torch.float64))
+        for x in cols:
+            cands.append(x.float().cuda())
+            cand_state.append(si)
+        cands.append(wide[:, si:si + 1])
+        cand_state.append(si)
+        cands.append((torch.randn(m, 2, generator=gen, dtype=torch.float64) * scale).float().cuda())
+        cand_state.append(si)
+    assert any(b.shape[1] == 1 and b.stride(0) > 1 for b in cands)
+    for eps in (0.1, 0.3):
+        _compare_scores(csvd, gst, cst, cand_state, cands, eps, "mixed", tail_floor=1e-6)
+    # every row filled: r_t = r = m, so a new column adds no direction
+    ms = 96
+    full = _oracle_states(ms, ms, [[b.cpu() for b in synth.random_blocks(ms, [60, 50], seed=3)]])
+    gfull = [_load(csvd, full[0])]
+    assert int(gfull[0].rank) == ms
+    col = [(torch.randn(ms, 1, generator=gen, dtype=torch.float64)).float().cuda() for _ in range(3)]
+    _compare_scores(csvd, gfull, full, [0, 0, 0], col, 0.2, "mixed", tail_floor=1e-6)
 
 
 def test_score_simt_and_tensor_gram_agree(csvd):

@@ -212,6 +212,254 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+K1_SHAPE = dict(n_states=256, per_state=256)
+
+
+def _k1_work(m, rt, r_new):
+    """Algorithmic work of one one-column evaluation: p = U^T a (2 m r_t),
+    ||a||^2 (2 m) and bisection of r_new eigenvalues from a bracket of width
+    at most ||G|| to 2.4e-7 ||G|| (22 halvings), 5 flops per term of the
+    O(r_t) inertia count; bytes: the candidate and its outputs."""
+    return dict(flops=2.0 * m * rt + 2.0 * m + 22.0 * r_new * 5.0 * rt,
+                bytes=4.0 * m + 17.0 + 4.0 * r_new)
+
+
+def run_reference_k1(args):
+    """The oracle on one-column candidates, timed on the host cores."""
+    from paper_2601_11626_gb300 import synth
+    from oracle import incremental as oinc
+
+    w = synth.scoring_k1(n_states=2, per_state=64, device="cpu")
+    m, r, eps = w["m"], w["r"], w["eps"]
+    st = oinc.IncrementalSVD(m, r)
+    st.append(w["states"][0][0])
+    rows = [w["Xt"][j].double().numpy().reshape(m, 1) for j in range(64)]
+    per_step = max(1, args.ref_sample) * 8
+    k = 0
+    for _ in range(args.warmup):
+        st.evaluate(rows[k % len(rows)], eps)
+        k += 1
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            st.evaluate(rows[k % len(rows)], eps)
+            k += 1
+            n += 1
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "one-column merge scoring (oracle sample)", "m": m, "r": r,
+                       "k": 1, "sample_per_step": per_step},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": v, "unit": UNIT,
+                             "sample": f"{per_step} one-column evaluations per step, one state"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_k1(args, world, rank, local):
+    """One-column (k = 1) merge scoring: 256 states (m = 768, r = 32, each
+    built from one 768 x 64 block, not timed) and 65,536 candidate vectors,
+    the rows of one matrix, 256 adjacent rows per state; one step scores all
+    of them through csvd_score_columns.  Inputs (201 MB) exceed L2."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2601_11626_gb300 import csvd, synth
+
+    dev = torch.cuda.current_device()
+    w = synth.scoring_k1(seed=rank, device="cuda", **K1_SHAPE)
+    m, r, eps = w["m"], w["r"], w["eps"]
+    states = []
+    for blocks in w["states"]:
+        st = csvd.IncrSVD(m, r)
+        for b in blocks:
+            st.append(b)
+        states.append(st)
+    torch.cuda.synchronize()
+    Xt = w["Xt"]
+    n = Xt.shape[0]
+    cs = w["cand_state"]
+    batch = csvd.ScoreColumns(states, cs, Xt, eps)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        batch.run()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        csvd.profile(True)
+        l0 = csvd.launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.run()
+        e1.record(stream)
+        e1.synchronize()
+        launches = csvd.launch_count() - l0
+        prof = csvd.profile_report()
+        csvd.profile(False)
+    ms = e0.elapsed_time(e1)
+    barrier()
+    value, ms = job_throughput(ms, n * args.steps, world)
+
+    peaks, _ = _peaks()
+    ranks = [s.rank for s in states]
+    work = [_k1_work(m, ranks[cs[j]], min(r, ranks[cs[j]] + 1)) for j in range(n)]
+    flops = sum(x["flops"] for x in work)
+    nl, tms = prof.get("core_arrow", (0, float("nan")))
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops * args.steps / (tms / 1000.0) / 1e12
+    roof = {"kernel": "core_arrow", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock",
+            "hbm_gbs": sum(x["bytes"] for x in work) * args.steps / (tms / 1000.0) / 1e9,
+            "kernels": {k: {"launches": v[0], "ms": v[1],
+                            "share": v[1] / sum(x[1] for x in prof.values())}
+                        for k, v in prof.items()}}
+
+    # plain FP32 form on the first 4096 candidates, for context
+    plain = None
+    if args.plain_steps > 0:
+        sub = 4096
+        pb = csvd.ScoreBatch(states, cs[:sub], [Xt[j].view(m, 1) for j in range(sub)], eps,
+                             "plain")
+        pb.run()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            pb.run()
+        p1.record(stream)
+        p1.synchronize()
+        pms = p0.elapsed_time(p1) / args.plain_steps
+        plain = {"value": world * sub / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+                 "candidates": sub,
+                 "max_tail_rel_diff_vs_mixed": float(((pb.tail.sqrt() - batch.tail[:sub].sqrt()).abs()
+                                                      / batch.tail[:sub].sqrt().clamp_min(1e-300)).max()),
+                 "accept_agree": bool((pb.accept == batch.accept[:sub]).all())}
+        del pb
+
+    # end to end: each step copies Xt from pinned host memory (second
+    # stream, double-buffered) and reads tail, accept and sigma back
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(Xt.shape, dtype=Xt.dtype, pin_memory=True)
+        host.copy_(Xt)
+        bufs = [Xt, torch.empty_like(Xt)]
+        batches = [batch, csvd.ScoreColumns(states, cs, bufs[1], eps)]
+        outs = [(torch.empty(batch.tail.shape, dtype=batch.tail.dtype, pin_memory=True),
+                 torch.empty(batch.accept.shape, dtype=batch.accept.dtype, pin_memory=True),
+                 torch.empty(batch.sigma.shape, dtype=batch.sigma.dtype, pin_memory=True))
+                for _ in range(2)]
+        out_bytes = batch.tail.numel() * 8 + batch.accept.numel() + batch.sigma.numel() * 4
+        copy_stream = torch.cuda.Stream()
+        ready = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for e in done:
+            e.record(stream)
+        for i in range(args.e2e_steps):
+            b = i % 2
+            copy_stream.wait_event(done[b])
+            with torch.cuda.stream(copy_stream):
+                bufs[b].copy_(host, non_blocking=True)
+                ready[b].record(copy_stream)
+            stream.wait_event(ready[b])
+            batches[b].run()
+            for o, src in zip(outs[b], (batches[b].tail, batches[b].accept, batches[b].sigma)):
+                o.copy_(src, non_blocking=True)
+            done[b].record(stream)
+        q1.record(stream)
+        q1.synchronize()
+        qms = q0.elapsed_time(q1) / args.e2e_steps
+        e2e_value, qms = job_throughput(qms, n, world)
+        in_bytes = Xt.numel() * Xt.element_size()
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": out_bytes, "ms_per_step": qms, "steps": args.e2e_steps,
+               "overlap": "inputs of step i copied on a second stream while step i-1 is scored"}
+        del batches, bufs
+
+    parity = None
+    if rank == 0 and args.parity_samples > 0:
+        from oracle import incremental as oinc
+        rng = np.random.default_rng(7)
+        idx = sorted(int(i) for i in rng.choice(n, args.parity_samples * 4, replace=False))
+        sig_d = batch.sigma.cpu().double().numpy()
+        tail_d = batch.tail.cpu().numpy()
+        acc_d = batch.accept.cpu().numpy()
+        worst_t, worst_s, flags, cache = 0.0, 0.0, 0, {}
+        for j in idx:
+            s_ = cs[j]
+            if s_ not in cache:
+                st = states[s_]
+                te = st.tail_error()
+                cache[s_] = oinc.IncrementalSVD(m, r, st.basis().double().cpu().numpy(),
+                                                st.sigma().astype(np.float64), te["energy"],
+                                                te["tail_sq"])
+            s_o, t_o, a_o, nxt = cache[s_].evaluate(Xt[j].reshape(m, 1).cpu(), eps)
+            worst_t = max(worst_t, abs(math.sqrt(tail_d[j]) - math.sqrt(nxt[3])) / math.sqrt(nxt[3]))
+            worst_s = max(worst_s, float(np.max(np.abs(sig_d[j, :len(s_o)] - s_o) / s_o[0])))
+            flags += int(bool(acc_d[j]) == a_o)
+        parity = {"sampled": len(idx), "max_tail_rel_err": worst_t,
+                  "max_sigma_err_rel_sigma1": worst_s, "accept_agree": flags,
+                  "reference": "FP64 oracle from the exported GPU states"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import incremental as oinc
+        st0 = oinc.IncrementalSVD(m, r)
+        st0.append(w["states"][0][0].cpu())
+        rows = [Xt[j].reshape(m, 1).cpu().double().numpy() for j in range(256)]
+        t0 = time.perf_counter()
+        done_n = 0
+        while time.perf_counter() - t0 < 10.0 and done_n < 4096:
+            st0.evaluate(rows[done_n % len(rows)], eps)
+            done_n += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": done_n / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done_n} one-column evaluations against one rebuilt state "
+                         f"(m={m}, r={r}), FP64 numpy, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"one-column merge scoring (k = 1 dataset shape): {len(states)} states "
+                            f"x {K1_SHAPE['per_state']} candidate vectors per GPU, m={m}, r={r}",
+                "m": m, "r": r, "k": 1, "n_candidates": n, "precision_form": "mixed", "eps": eps,
+                "l2": "inputs (%.2f GB) larger than L2, no flush" % (Xt.numel() * 4 / 1e9),
+                "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
+            "plain_fp32": plain, "parity": parity, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    for st in states:
+        st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,12 +475,18 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parity-samples", type=int, default=8)
+    ap.add_argument("--k1", action="store_true",
+                    help="one-column candidates (the k = 1 dataset shape) through "
+                         "csvd_score_columns instead of the uneven-width batch")
     args = ap.parse_args()
 
     world, rank, local = _dist()
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args)
+            run_reference_k1(args) if args.k1 else run_reference(args)
+        return
+    if args.k1:
+        run_k1(args, world, rank, local)
         return
 
     import torch

@@ -136,6 +136,25 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
                        float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
                        double* tail_paper_out, uint8_t* accept_out);
 
+/* Batched merge evaluation of one-column candidates (blocks of width 1,
+ * the k = 1 regime of the evaluation section's dataset table) given as the
+ * rows of one matrix: candidate j is the column a_j = Xt[j * ldx + i],
+ * i < m (Xt: n x m row-major f32, DEVICE, ldx >= m), tentatively appended
+ * to states[cand_state[j]] (cand_state: n entries on the HOST; NULL means
+ * state 0).  Outputs as in csvd_score, indexed by j (DEVICE; tail_paper_out
+ * and accept_out may be NULL).  Mixed form only: with k = 1 the Gram of the
+ * core (Lemma 1) is the arrowhead [[diag(sigma^2), sigma * p], [., ||a||^2]]
+ * with p = U^T a, whose top eigenvalues are found by bisection on its exact
+ * inertia count.  Rows whose state has r_t > 128 take the general mixed
+ * path.  Adjacent rows of one state share each read of its basis (up to
+ * four at a time), so order the rows by state where possible.  The host
+ * arrays may be reused on return; stream-ordered on the stream of
+ * states[0]; no state is modified. */
+csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
+                               const int32_t* cand_state, const float* Xt, int64_t ldx, int32_t n,
+                               double eps, float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                               double* tail_paper_out, uint8_t* accept_out);
+
 /* Bounds for blocks taken in the given order (Section 3):
  *   weyl_sq     Thm. 1: sum ||A_j||^2 - max_j sum_{i<=r} sigma_i^2(A_j)
  *   residual_sq Cor. 1: sum ||A_j||^2 - sum_{j<=r} mu_j^2, mu the singular

@@ -404,10 +404,14 @@ static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, c
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return reinterpret_cast<uintptr_t>(items[x].st.U) < reinterpret_cast<uintptr_t>(items[y].st.U);
   });
+  auto same_state = [&](const Item& x, const Item& y) {
+    return x.st.U == y.st.U && x.st.ldu == y.st.ldu && x.st.rt == y.st.rt && x.r == y.r &&
+           x.m == y.m && x.st.sigma == y.st.sigma && x.st.scal == y.st.scal;
+  };
   std::vector<int2> groups;
   for (int i = 0; i < n; ++i) {
     if (groups.empty() || groups.back().y == kArrowGroup ||
-        items[order[i]].st.U != items[order[groups.back().x]].st.U)
+        !same_state(items[order[i]], items[order[groups.back().x]]))
       groups.push_back(make_int2(i, 0));
     ++groups.back().y;
   }
@@ -971,6 +975,78 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
   }
   Workspace ws;
   return run_items(items, eps, precision, s, states[0]->status, ws, nullptr, false);
+}
+
+csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
+                               const int32_t* cand_state, const float* Xt, int64_t ldx, int32_t n,
+                               double eps, float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                               double* tail_paper_out, uint8_t* accept_out) {
+  if (!states || n_states < 1 || n < 0 || (n > 0 && (!Xt || !sigma_out || !tail_sq_out)))
+    return fail(CSVD_ERR_ARG, "NULL argument");
+  if (n == 0) return CSVD_OK;
+  const int64_t m = states[0]->m;
+  if (ldx < m) return fail(CSVD_ERR_ARG, "ldx < m");
+  cudaStream_t s = states[0]->stream;
+  std::vector<ArrowState> tab(n_states);
+  std::vector<char> arrow_ok(n_states, 0);
+  for (int i = 0; i < n_states; ++i) {
+    if (!states[i]) return fail(CSVD_ERR_ARG, "NULL state");
+    if (states[i]->m != m) return fail(CSVD_ERR_SHAPE, "states differ in m");
+    const StateView v = view_of(states[i]);
+    tab[i] = ArrowState{v.U, v.ldu, m, v.rt,
+                        (int)std::min<int64_t>(v.r, v.rt + std::min<int64_t>(1, m - v.rt)),
+                        v.sigma, v.scal};
+    arrow_ok[i] = v.rt <= kArrowMaxRt;
+  }
+  // runs of adjacent rows of one state, up to kArrowGroup per CTA; rows of
+  // states past the one-column core's limit take the general path
+  std::vector<int4> groups;
+  std::vector<csvd_block> rest_blocks;
+  std::vector<int> rest_rows;
+  for (int j = 0; j < n; ++j) {
+    const int si = cand_state ? cand_state[j] : 0;
+    if (si < 0 || si >= n_states) return fail(CSVD_ERR_ARG, "bad cand_state");
+    if (ld_sigma < states[si]->r) return fail(CSVD_ERR_ARG, "ld_sigma < r");
+    if (!arrow_ok[si]) {
+      rest_blocks.push_back(csvd_block{Xt + (int64_t)j * ldx, 1, 1, CSVD_F32, 0});
+      rest_rows.push_back(j);
+      continue;
+    }
+    if (groups.empty() || groups.back().z != si || groups.back().y == kArrowGroup ||
+        groups.back().x + groups.back().y != j)
+      groups.push_back(make_int4(j, 0, si, 0));
+    ++groups.back().y;
+  }
+  if (!groups.empty()) {
+    const size_t tab_bytes = sizeof(ArrowState) * n_states, grp_bytes = sizeof(int4) * groups.size();
+    const size_t grp_off = (tab_bytes + 15) & ~size_t(15);
+    std::vector<char> host(grp_off + grp_bytes, 0);
+    std::memcpy(host.data(), tab.data(), tab_bytes);
+    std::memcpy(host.data() + grp_off, groups.data(), grp_bytes);
+    Workspace w;
+    w.s = s;
+    w.base = static_cast<char*>(dev_alloc(host.size(), s));
+    if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+    CUDA_TRY(upload(w.base, host.data(), host.size(), s));
+    CUDA_TRY(launch_core_arrow_columns(w.at<ArrowState>(0), w.at<int4>(grp_off),
+                                       (int)groups.size(), Xt, ldx, sigma_out, ld_sigma,
+                                       tail_sq_out, tail_paper_out, accept_out, eps,
+                                       states[0]->status, s));
+  }
+  if (!rest_rows.empty()) {
+    std::vector<Item> items(rest_rows.size());
+    for (size_t i = 0; i < rest_rows.size(); ++i) {
+      const int j = rest_rows[i];
+      const int si = cand_state ? cand_state[j] : 0;
+      items[i] = Item{view_of(states[si]), &rest_blocks[i], states[si]->r, m,
+                      sigma_out + (int64_t)j * ld_sigma, tail_sq_out + j,
+                      tail_paper_out ? tail_paper_out + j : nullptr, nullptr,
+                      accept_out ? accept_out + j : nullptr};
+    }
+    Workspace ws;
+    CSVD_TRY(run_items_general(items, eps, CSVD_MIXED, s, states[0]->status, ws, nullptr, false));
+  }
+  return CSVD_OK;
 }
 
 }  // extern "C"

@@ -115,6 +115,15 @@ struct ArrowDesc {
   uint8_t* accept_out;     // may be null
   double eps;
 };
+// One state as the one-column path reads it.
+struct ArrowState {
+  const float* U;
+  int64_t ldu;
+  int64_t m;
+  int rt, r_new;
+  const float* sigma;
+  const double* scal;
+};
 
 // ------------------------------------------------------------ energy
 struct EnergyDesc {
@@ -192,6 +201,14 @@ cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, in
                                 int* d_status, cudaStream_t s);
 cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
                               int* d_status, cudaStream_t s);
+// Candidates as rows of one matrix: group g = {first row, count, state, 0};
+// row j of Xt (ldx floats apart) is candidate j, whose outputs sit at index
+// j of the output arrays (sigma rows ld_sigma apart; paper, accept may be null).
+cudaError_t launch_core_arrow_columns(const ArrowState* d_states, const int4* d_groups,
+                                      int n_groups, const float* Xt, int64_t ldx,
+                                      float* sigma_out, int64_t ld_sigma, double* tail_out,
+                                      double* tail_paper_out, uint8_t* accept_out, double eps,
+                                      int* d_status, cudaStream_t s);
 cudaError_t launch_gram_dev(const float* U, int64_t ldu, int m, int r, float* D, cudaStream_t s);
 cudaError_t launch_state_commit(const float* sigma_new, int r_new, float* sigma,
                                 const double* energy_new, const double* tail_new,

@@ -16,7 +16,9 @@
 //
 // One 128-thread CTA per group of up to kArrowGroup candidates of the same
 // state: rows of the group's columns are staged in shared memory 128 at a
-// time and every row of U read from L2 serves the whole group.
+// time and every row of U read from L2 serves the whole group.  Two entry
+// kernels fill the group's view (a descriptor per candidate, or candidates
+// as the rows of one matrix with outputs indexed by row) and share the body.
 #include "common.cuh"
 
 namespace csvd {
@@ -41,17 +43,29 @@ __device__ __forceinline__ int arrow_count(const float* d, const float* z2, int 
   return c + (s < 0.f);
 }
 
-}  // namespace
+// What one CTA evaluates: a state and up to kArrowGroup candidates of it.
+struct ArrowGroupView {
+  const float* U;
+  const float* sigma;
+  const double* scal;
+  int64_t ldu, m;
+  int rt, rq, cnt;
+  double eps;
+  const float* a[kArrowGroup];
+  int64_t lda[kArrowGroup];
+  float* sigma_out[kArrowGroup];
+  double* tail_out[kArrowGroup];
+  double* paper_out[kArrowGroup];   // may be null
+  double* energy_out[kArrowGroup];  // may be null
+  uint8_t* accept_out[kArrowGroup]; // may be null
+};
 
-__global__ void __launch_bounds__(kArrowThreads)
-core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ groups,
-                  int* __restrict__ status) {
-  const int2 gr = groups[blockIdx.x];
-  const ArrowDesc* D = descs + gr.x;
-  const int cnt = gr.y;
-  const int rt = D[0].rt, n = rt + 1, rq = D[0].r_new;
-  const int64_t m = D[0].m, ldu = D[0].ldu;
-  const float* __restrict__ U = D[0].U;
+__device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __restrict__ status) {
+  const int cnt = V.cnt;
+  const int rt = V.rt, n = rt + 1, rq = V.rq;
+  const int64_t m = V.m, ldu = V.ldu;
+  const float* __restrict__ U = V.U;
+  const float* __restrict__ sigma = V.sigma;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
   __shared__ float4 s_a[kArrowThreads];
@@ -67,8 +81,8 @@ core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ 
   int64_t lda[kArrowGroup];
 #pragma unroll
   for (int g = 0; g < kArrowGroup; ++g) {
-    ap[g] = g < cnt ? D[g].a : nullptr;
-    lda[g] = g < cnt ? D[g].lda : 0;
+    ap[g] = g < cnt ? V.a[g] : nullptr;
+    lda[g] = g < cnt ? V.lda[g] : 0;
   }
 
   // 1. p = U^T a for every candidate and ||a||^2 (FP64 totals).  The r_t
@@ -121,9 +135,9 @@ core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ 
   bool sorted_ok = true;
   if (tid < rt) {
     const int sl = tid / 32, ln = tid % 32;
-    const float sj = D[0].sigma[tid];
+    const float sj = sigma[tid];
     s_d[tid] = sj * sj;
-    if (tid + 1 < rt) sorted_ok = sj >= D[0].sigma[tid + 1];
+    if (tid + 1 < rt) sorted_ok = sj >= sigma[tid + 1];
 #pragma unroll
     for (int g = 0; g < kArrowGroup; ++g) {
       float p = 0.f;
@@ -214,28 +228,100 @@ core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ 
   // 4. FP64 epilogue (warp g <-> candidate g): sigma~, tail from the trace,
   //    energy, accept flag
   if (wid < cnt) {
-    const ArrowDesc& dsc = D[wid];
     const double alpha_d = s_alpha[wid];
+    float* sig_out = V.sigma_out[wid];
     double top = 0.0, tr = 0.0;
     for (int q = lane; q < rq; q += 32) {
       top += (double)s_lam[wid][q];
-      dsc.sigma_out[q] = sqrtf(fmaxf(s_lam[wid][q], 0.f));
+      sig_out[q] = sqrtf(fmaxf(s_lam[wid][q], 0.f));
     }
     for (int j = lane; j < rt; j += 32) tr += (double)s_d[j];
     top = warp_sum_d(top);
     tr = warp_sum_d(tr) + alpha_d;
     if (lane == 0) {
-      const double energy_new = dsc.scal[0] + alpha_d;
-      double tail = dsc.scal[1] + (tr - top);
+      const double energy_new = V.scal[0] + alpha_d;
+      double tail = V.scal[1] + (tr - top);
       if (tail < 0.0) tail = 0.0;
       double paper = energy_new - top;
       if (paper < 0.0) paper = 0.0;
-      dsc.tail_out[0] = tail;
-      if (dsc.tail_paper_out) dsc.tail_paper_out[0] = paper;
-      if (dsc.energy_out) dsc.energy_out[0] = energy_new;
-      if (dsc.accept_out) dsc.accept_out[0] = (tail <= dsc.eps * dsc.eps * energy_new) ? 1 : 0;
+      V.tail_out[wid][0] = tail;
+      if (V.paper_out[wid]) V.paper_out[wid][0] = paper;
+      if (V.energy_out[wid]) V.energy_out[wid][0] = energy_new;
+      if (V.accept_out[wid]) V.accept_out[wid][0] = (tail <= V.eps * V.eps * energy_new) ? 1 : 0;
     }
   }
+}
+
+}  // namespace
+
+// A descriptor per candidate; group = {first descriptor, count}.
+__global__ void __launch_bounds__(kArrowThreads)
+core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ groups,
+                  int* __restrict__ status) {
+  __shared__ ArrowGroupView V;
+  const int2 gr = groups[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    const ArrowDesc& d = descs[gr.x];
+    V.U = d.U;
+    V.sigma = d.sigma;
+    V.scal = d.scal;
+    V.ldu = d.ldu;
+    V.m = d.m;
+    V.rt = d.rt;
+    V.rq = d.r_new;
+    V.cnt = gr.y;
+    V.eps = d.eps;
+  }
+  if (t < kArrowGroup) {
+    const bool on = t < gr.y;
+    const ArrowDesc* d = on ? descs + gr.x + t : nullptr;
+    V.a[t] = on ? d->a : nullptr;
+    V.lda[t] = on ? d->lda : 0;
+    V.sigma_out[t] = on ? d->sigma_out : nullptr;
+    V.tail_out[t] = on ? d->tail_out : nullptr;
+    V.paper_out[t] = on ? d->tail_paper_out : nullptr;
+    V.energy_out[t] = on ? d->energy_out : nullptr;
+    V.accept_out[t] = on ? d->accept_out : nullptr;
+  }
+  __syncthreads();
+  arrow_group(V, status);
+}
+
+// Candidates as rows of Xt; group = {first row, count, state, unused}.
+__global__ void __launch_bounds__(kArrowThreads)
+core_arrow_columns_kernel(const ArrowState* __restrict__ states, const int4* __restrict__ groups,
+                          const float* __restrict__ Xt, int64_t ldx, float* sigma_out,
+                          int64_t ld_sigma, double* tail_out, double* paper_out,
+                          uint8_t* accept_out, double eps, int* __restrict__ status) {
+  __shared__ ArrowGroupView V;
+  const int4 gr = groups[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    const ArrowState& st = states[gr.z];
+    V.U = st.U;
+    V.sigma = st.sigma;
+    V.scal = st.scal;
+    V.ldu = st.ldu;
+    V.m = st.m;
+    V.rt = st.rt;
+    V.rq = st.r_new;
+    V.cnt = gr.y;
+    V.eps = eps;
+  }
+  if (t < kArrowGroup) {
+    const bool on = t < gr.y;
+    const int64_t j = (int64_t)gr.x + t;
+    V.a[t] = on ? Xt + j * ldx : nullptr;
+    V.lda[t] = 1;
+    V.sigma_out[t] = on ? sigma_out + j * ld_sigma : nullptr;
+    V.tail_out[t] = on ? tail_out + j : nullptr;
+    V.paper_out[t] = on && paper_out ? paper_out + j : nullptr;
+    V.energy_out[t] = nullptr;
+    V.accept_out[t] = on && accept_out ? accept_out + j : nullptr;
+  }
+  __syncthreads();
+  arrow_group(V, status);
 }
 
 cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
@@ -243,6 +329,20 @@ cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int
   if (n_groups <= 0) return cudaSuccess;
   prof_begin(s);
   core_arrow_kernel<<<n_groups, kArrowThreads, 0, s>>>(d_desc, d_groups, d_status);
+  prof_end("core_arrow", s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core_arrow_columns(const ArrowState* d_states, const int4* d_groups,
+                                      int n_groups, const float* Xt, int64_t ldx,
+                                      float* sigma_out, int64_t ld_sigma, double* tail_out,
+                                      double* tail_paper_out, uint8_t* accept_out, double eps,
+                                      int* d_status, cudaStream_t s) {
+  if (n_groups <= 0) return cudaSuccess;
+  prof_begin(s);
+  core_arrow_columns_kernel<<<n_groups, kArrowThreads, 0, s>>>(
+      d_states, d_groups, Xt, ldx, sigma_out, ld_sigma, tail_out, tail_paper_out, accept_out, eps,
+      d_status);
   prof_end("core_arrow", s);
   return cudaGetLastError();
 }

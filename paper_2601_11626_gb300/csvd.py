@@ -63,6 +63,7 @@ def _sig(lib):
     lib.csvd_tail_error.argtypes = [VP, P(D), P(D), P(D), P(D)]
     lib.csvd_incr_free.argtypes = [VP]
     lib.csvd_score.argtypes = [P(VP), I32, P(I32), P(Block), I32, D, I32, VP, I64, VP, VP, VP]
+    lib.csvd_score_columns.argtypes = [P(VP), I32, P(I32), VP, I64, I32, D, VP, I64, VP, VP, VP]
     lib.csvd_bounds.argtypes = [P(Block), I32, I64, I32, VP, P(D), P(D), P(D), P(D)]
     lib.csvd_cluster.argtypes = [P(Block), I32, I64, I32, D, I32, I32, I32, VP, P(I32), P(D),
                                  P(D), P(D)]
@@ -78,7 +79,7 @@ def _sig(lib):
     lib.csvd_profile_report.restype = C.c_int
     for name in ("csvd_incr_init", "csvd_incr_append", "csvd_incr_sigma", "csvd_incr_basis",
                  "csvd_incr_load", "csvd_gram_apply",
-                 "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_bounds",
+                 "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_score_columns", "csvd_bounds",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator"):
         getattr(lib, name).restype = C.c_int
 
@@ -248,6 +249,44 @@ class ScoreBatch:
                                     C.c_void_p(self.paper.data_ptr()),
                                     C.c_void_p(self.accept.data_ptr())))
         return self
+
+
+class ScoreColumns:
+    """Repeated ``csvd_score_columns`` calls: one-column candidates given as
+    the rows of ``Xt`` (n x m, f32, CUDA, unit column stride), candidate j
+    scored against ``states[cand_state[j]]`` in the mixed form."""
+
+    def __init__(self, states, cand_state, Xt, eps, r_max=None):
+        if Xt.dtype != torch.float32 or not Xt.is_cuda or Xt.dim() != 2 or Xt.stride(1) != 1:
+            raise ValueError("Xt must be a CUDA float32 matrix with unit column stride")
+        self._lib = lib()
+        self.states = states
+        self.Xt = Xt
+        self.n = Xt.shape[0]
+        self.eps = float(eps)
+        self._st = (C.c_void_p * len(states))(*[s.handle.value for s in states])
+        self._cs = (C.c_int32 * self.n)(*[int(x) for x in cand_state])
+        self.r_max = r_max or max(s.r for s in states)
+        self.sigma = torch.zeros(self.n, self.r_max, device="cuda", dtype=torch.float32)
+        self.tail = torch.zeros(self.n, device="cuda", dtype=torch.float64)
+        self.paper = torch.zeros(self.n, device="cuda", dtype=torch.float64)
+        self.accept = torch.zeros(self.n, device="cuda", dtype=torch.uint8)
+
+    def run(self):
+        _check(self._lib.csvd_score_columns(self._st, len(self.states), self._cs,
+                                            C.c_void_p(self.Xt.data_ptr()), self.Xt.stride(0),
+                                            self.n, self.eps, C.c_void_p(self.sigma.data_ptr()),
+                                            self.r_max, C.c_void_p(self.tail.data_ptr()),
+                                            C.c_void_p(self.paper.data_ptr()),
+                                            C.c_void_p(self.accept.data_ptr())))
+        return self
+
+
+def score_columns(states, cand_state, Xt, eps):
+    """One-column candidates (rows of ``Xt``); returns (sigma, tail_sq,
+    tail_paper, accept) as CUDA tensors."""
+    b = ScoreColumns(states, cand_state, Xt, eps).run()
+    return b.sigma, b.tail, b.paper, b.accept
 
 
 def score(states, cand_state, cands, eps, precision="mixed"):

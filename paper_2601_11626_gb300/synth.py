@@ -178,6 +178,42 @@ def scoring_c4(r=64, seed=0, device="cpu", n_states=64, appends=8, per_state=64,
                 cand_latent=c_assign, pools=(st_pool, c_pool), eps=0.05)
 
 
+def scoring_k1(seed=0, device="cpu", n_states=256, per_state=256, m=768, r=32, build=64,
+               d=24, decay=0.9, noise=5e-2, w_max=0.3, eps=0.2):
+    """One-column merge scoring with the k = 1 dataset's shape (768-dim
+    vectors, r = 32, eps = 0.2): ``n_states`` latent m x d subspaces with
+    spectrum ``decay``^i; state s is built from one m x ``build`` block of
+    subspace s; candidate j (row j of the returned n x m matrix ``Xt``) is
+    a vector of subspace j mod n_states plus a second subspace with weight
+    U[0, w_max] and Gaussian noise, scored against state j // per_state (rows
+    of one state are adjacent).  Vectorised per subspace; same recipe as
+    ``latent_mixture`` with k = 1."""
+    bases = latent_bases(m, d, n_states, seed)
+    B = torch.stack([b.to(torch.float32) for b in bases]).to(device)       # n_states x m x d
+    spec = torch.tensor([decay ** i for i in range(d)], dtype=torch.float32, device=device)
+    g = _gen(seed, 31, device=device)
+    st_coef = torch.randn(n_states, d, build, generator=g, device=device) * spec[None, :, None]
+    st_blocks = torch.bmm(B, st_coef)
+    st_blocks += noise * torch.randn(st_blocks.shape, generator=g, device=device)
+    n = n_states * per_state
+    c1 = torch.arange(n, device=device) % n_states
+    gc = _gen(seed, 32, device="cpu")
+    c2 = (c1.cpu() + 1 + torch.randint(0, n_states - 1, (n,), generator=gc)) % n_states
+    w = torch.rand(n, generator=gc) * w_max
+    coef1 = torch.randn(n, d, generator=g, device=device) * spec
+    coef2 = torch.randn(n, d, generator=g, device=device) * spec * w.to(device)[:, None]
+    Xt = noise * torch.randn(n, m, generator=g, device=device)
+    c2 = c2.to(device)
+    for c in range(n_states):
+        rows = (c1 == c).nonzero().squeeze(1)
+        Xt[rows] += coef1[rows] @ B[c].T
+        rows2 = (c2 == c).nonzero().squeeze(1)
+        Xt[rows2] += coef2[rows2] @ B[c].T
+    cand_state = [j // per_state for j in range(n)]
+    return dict(m=m, r=r, eps=eps, states=[[st_blocks[s]] for s in range(n_states)], Xt=Xt,
+                cand_state=cand_state, cand_latent=c1.tolist())
+
+
 def grad_c5(seed=0, device="cpu", n_blocks=1024, m=2048, k=256, fd_blocks=8):
     """Blocks 2048x256 from 32 latent subspaces of dimension 48.  Each latent
     spectrum has a strong head (43 directions, 42 for every third subspace)

@@ -211,6 +211,46 @@ def test_score_one_column_arrowhead(csvd):
     _compare_scores(csvd, gfull, full, [0, 0, 0], col, 0.2, "mixed", tail_floor=1e-6)
 
 
+def test_score_columns_against_oracle(csvd):
+    """``csvd_score_columns``: one-column candidates as the rows of one
+    matrix (row pitch > m), states with r_t = 0, 24, 128 and 160 (the last
+    through the general mixed path), runs of one state of lengths 1 to 7
+    between interleaved rows, each row checked against the oracle."""
+    m = 768
+    specs = [(32, []), (24, [16, 24]), (128, [96, 64]), (160, [120, 80])]
+    cst, gst = [], []
+    for r, widths in specs:
+        raw = [b.cpu() for b in synth.random_blocks(m, widths, seed=r + 1, decay=0.97)] if widths else []
+        cst += _oracle_states(m, r, [raw])
+        gst.append(_load(csvd, cst[-1]))
+    assert [int(g.rank) for g in gst] == [0, 24, 128, 160]
+    cand_state = [1] * 7 + [2] * 5 + [0] * 2 + [3] * 4 + [0, 1, 2, 3] * 3 + [2] * 1 + [1] * 6
+    n = len(cand_state)
+    gen = torch.Generator().manual_seed(9)
+    rows = []
+    for j, si in enumerate(cand_state):
+        c = cst[si]
+        scale = math.sqrt(max(c.energy, 1.0) / m)
+        x = torch.randn(m, generator=gen, dtype=torch.float64) * scale
+        if j % 3 == 0 and c.Q.shape[1] > 0:   # mostly inside the state's span
+            w = torch.randn(c.Q.shape[1], generator=gen, dtype=torch.float64)
+            x = torch.tensor(c.Q) @ (w * torch.tensor(c.s)) + 1e-2 * x
+        rows.append(x)
+    Xpad = torch.zeros(n, m + 12, dtype=torch.float32, device="cuda")
+    Xpad[:, :m] = torch.stack(rows).float().cuda()
+    Xt = Xpad[:, :m]
+    assert Xt.stride(0) == m + 12
+    for eps in (0.1, 0.3):
+        sig, tail, paper, acc = csvd.score_columns(gst, cand_state, Xt, eps)
+        sig, tail, acc = _np(sig), _np(tail), acc.cpu().numpy()
+        for j, si in enumerate(cand_state):
+            s_o, t_o, a_o, nxt = cst[si].evaluate(Xt[j].reshape(m, 1).cpu(), eps)
+            _check_sigma(sig[j, :len(s_o)], s_o, mixed=True)
+            _check_tail(tail[j], nxt[3], floor=math.sqrt(1e-6 * nxt[2]))
+            if abs(math.sqrt(t_o / nxt[2]) - eps) > 1e-3 * eps:
+                assert bool(acc[j]) == a_o, (j, acc[j], a_o)
+
+
 def test_score_simt_and_tensor_gram_agree(csvd):
     """The same candidates through the tensor-core Gram (16-byte aligned rows)
     and the SIMT fallback (odd leading dimension) against the oracle."""

@@ -217,10 +217,11 @@ K1_SHAPE = dict(n_states=256, per_state=256)
 
 def _k1_work(m, rt, r_new):
     """Algorithmic work of one one-column evaluation: p = U^T a (2 m r_t),
-    ||a||^2 (2 m) and bisection of r_new eigenvalues from a bracket of width
-    at most ||G|| to 2.4e-7 ||G|| (22 halvings), 5 flops per term of the
-    O(r_t) inertia count; bytes: the candidate and its outputs."""
-    return dict(flops=2.0 * m * rt + 2.0 * m + 22.0 * r_new * 5.0 * rt,
+    ||a||^2 (2 m) and r_new roots of the arrowhead's secular equation at 4
+    evaluations each (a fast-converging zero finder), 6 flops per term of the
+    O(r_t) secular sum and its derivative; bytes: the candidate and its
+    outputs."""
+    return dict(flops=2.0 * m * rt + 2.0 * m + 4.0 * r_new * 6.0 * rt,
                 bytes=4.0 * m + 17.0 + 4.0 * r_new)
 
 

@@ -9,14 +9,30 @@
 //     #{lambda < x} = #{j : d_j < x} + [alpha - x - sum_j z_j^2 / (d_j - x) < 0],
 // an exact O(r_t) count.  Multisection bisection on it gives the top r_new
 // eigenvalues (sigma~_j = sqrt(lambda_j), Cor. 3) and the tail follows from
-// the trace, tr(G) - sum of the top, in FP64.  diag(d) is the leading
-// principal block of G, so (Cauchy interlacing) with s non-increasing the
-// q-th largest eigenvalue lies in [d_q, d_{q-1}]: that bracket, not the whole
-// Gershgorin interval, starts its bisection.
+// the trace, tr(G) - sum of the top, in FP64.
+//
+// diag(d) is the leading principal block of G, so (Cauchy interlacing) with
+// s non-increasing the q-th largest eigenvalue lies in [d_q, d_{q-1}] (ends
+// closed by the Gershgorin interval).  Inside that bracket no pole lies
+// between x and the root, the count is (r_t - q) + [f(x) < 0] with the
+// secular function f(x) = alpha - x - sum_j z_j^2 / (d_j - x), and f is
+// decreasing; each evaluation narrows the bracket by the sign of f and
+// proposes the next point from a rational model fitted to f and f' at x:
+//   interior brackets: one pole (the end nearer the bracket's centre),
+//     f ~ A + B / (pole - y)                       -> y = pole + B / A;
+//   end brackets (no pole beyond the top / below the bottom eigenvalue):
+//     f ~ C - y - E / (pole - y), linear term kept -> a quadratic in y.
+// A proposal outside the bracket is replaced by the midpoint; once proposals
+// have run kArrowModelIters times the rest is plain bisection, so every
+// eigenvalue ends within 16 + 24 evaluations.  States whose sigma is not
+// sorted fall back to multisection bisection on the full inertia count over
+// the Gershgorin interval.
 //
 // One 128-thread CTA per group of up to kArrowGroup candidates of the same
-// state: rows of the group's columns are staged in shared memory 128 at a
-// time and every row of U read from L2 serves the whole group.  Two entry
+// state: rows of the group's columns are staged in shared memory up to 1024
+// at a time (all loads of a pass in flight together) and every row of U read
+// from L2 serves the whole group.  ||a||^2 is accumulated per thread as a
+// compensated FP32 pair and only the per-thread totals are added in FP64.  Two entry
 // kernels fill the group's view (a descriptor per candidate, or candidates
 // as the rows of one matrix with outputs indexed by row) and share the body.
 #include "common.cuh"
@@ -27,6 +43,9 @@ namespace {
 constexpr int kArrowThreads = 128;
 constexpr int kArrowWarps = kArrowThreads / 32;
 constexpr int kArrowBisectMax = 64;
+constexpr int kArrowModelIters = 16;
+constexpr int kArrowStage = 512;  // rows of the group's columns staged per pass
+constexpr int kArrowPerThread = kArrowStage / kArrowThreads;
 static_assert(kArrowGroup == 4, "rows of the group are staged as float4");
 static_assert(kArrowGroup <= kArrowWarps, "one warp per candidate in the per-item steps");
 
@@ -41,6 +60,25 @@ __device__ __forceinline__ int arrow_count(const float* d, const float* z2, int 
     s -= __fdividef(z2[j], q);
   }
   return c + (s < 0.f);
+}
+
+// s + c += v^2 with the square split exactly (v^2 = p + e) and the sum
+// compensated (Knuth's two-sum): a double-float accumulator in FP32 pipes.
+__device__ __forceinline__ void arrow_acc_sq(float& s, float& c, float v) {
+  const float p = v * v;
+  const float e = fmaf(v, v, -p);
+  const float t = s + p;
+  const float bp = t - s;
+  c += ((s - (t - bp)) + (p - bp)) + e;
+  s = t;
+}
+
+// Root t of t^2 - h t - E = 0 (E >= 0): the non-negative one if `positive`,
+// else the non-positive one, each in a form free of cancellation.
+__device__ __forceinline__ float arrow_quad_root(float h, float E, bool positive) {
+  const float sq = sqrtf(fmaf(h, h, 4.f * E));
+  if (positive) return h >= 0.f ? 0.5f * (h + sq) : (2.f * E) / (sq - h);
+  return h <= 0.f ? 0.5f * (h - sq) : (-2.f * E) / (sq + h);
 }
 
 // What one CTA evaluates: a state and up to kArrowGroup candidates of it.
@@ -68,10 +106,11 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   const float* __restrict__ sigma = V.sigma;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
-  __shared__ float4 s_a[kArrowThreads];
+  __shared__ float4 s_a[kArrowStage];
   __shared__ float s_part[kArrowWarps][kArrowGroup][32];
   __shared__ float s_d[kArrowMaxRt];
   __shared__ float s_z2[kArrowGroup][kArrowMaxRt];
+  __shared__ float2 s_dz[kArrowGroup][kArrowMaxRt];  // {d_j, z_j^2}
   __shared__ float s_lam[kArrowGroup][kArrowMaxRt + 1];
   __shared__ float s_lo[kArrowGroup], s_hi[kArrowGroup];
   __shared__ double s_red[kArrowWarps][kArrowGroup];
@@ -94,21 +133,28 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   const int col = slab * 32 + lane;
   const bool pj_on = nslab > 0 && rg < nrg && col < rt;
   float acc[kArrowGroup] = {};
-  double aa[kArrowGroup] = {};
-  for (int64_t i0 = 0; i0 < m; i0 += kArrowThreads) {
-    const int64_t i = i0 + tid;
-    float v[kArrowGroup];
+  float es[kArrowGroup] = {}, ec[kArrowGroup] = {};
+  for (int64_t i0 = 0; i0 < m; i0 += kArrowStage) {
+    const int len = (int)(m - i0 < kArrowStage ? m - i0 : kArrowStage);
+    // every load of the pass is issued before any is used
+    float v[kArrowPerThread][kArrowGroup];
 #pragma unroll
-    for (int g = 0; g < kArrowGroup; ++g) {
-      v[g] = (g < cnt && i < m) ? ap[g][i * lda[g]] : 0.f;
-      aa[g] = fma((double)v[g], (double)v[g], aa[g]);
+    for (int k = 0; k < kArrowPerThread; ++k) {
+      const int ii = tid + k * kArrowThreads;
+#pragma unroll
+      for (int g = 0; g < kArrowGroup; ++g)
+        v[k][g] = (g < cnt && ii < len) ? ap[g][(i0 + ii) * lda[g]] : 0.f;
     }
-    s_a[tid] = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int k = 0; k < kArrowPerThread; ++k) {
+      s_a[tid + k * kArrowThreads] = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
+#pragma unroll
+      for (int g = 0; g < kArrowGroup; ++g) arrow_acc_sq(es[g], ec[g], v[k][g]);
+    }
     __syncthreads();
     if (pj_on) {
-      const int len = (int)(m - i0 < kArrowThreads ? m - i0 : kArrowThreads);
       const float* u = U + i0 * ldu + col;
-#pragma unroll 8
+#pragma unroll 16
       for (int ii = rg; ii < len; ii += nrg) {
         const float uu = __ldg(u + (int64_t)ii * ldu);
         const float4 x = s_a[ii];
@@ -123,7 +169,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
 #pragma unroll
   for (int g = 0; g < kArrowGroup; ++g) {
     s_part[wid][g][lane] = acc[g];
-    const double t = warp_sum_d(aa[g]);
+    const double t = warp_sum_d((double)es[g] + (double)ec[g]);
     if (lane == 0) s_red[wid][g] = t;
   }
   __syncthreads();
@@ -144,6 +190,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
       for (int r2 = 0; r2 < nrg; ++r2) p += s_part[r2 * nslab + sl][g][ln];
       const float zj = sj * p;
       s_z2[g][tid] = zj * zj;
+      s_dz[g][tid] = make_float2(sj * sj, zj * zj);
     }
   }
   const bool sorted = __syncthreads_and(sorted_ok);
@@ -171,56 +218,136 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   }
   __syncthreads();
 
-  // 3. multisection bisection: one task per (candidate, eigenvalue), g
-  //    threads per task
+  // 3. one task per (candidate, eigenvalue)
   const int ntask = cnt * rq;
-  int g = 1;
-  while (g < 16 && g * 2 * ntask <= kArrowThreads) g *= 2;
-  const int ngroups = kArrowThreads / g;
-  const int grp = tid / g, sub = tid % g;
-  const unsigned shift = (unsigned)((lane / g) * g);
-  const unsigned gmask = ((1u << g) - 1u) << shift;
   int capped = 0;
-  for (int t0 = 0; t0 < ntask; t0 += ngroups) {  // uniform trip count across the block
-    const int t = t0 + grp;
-    const bool active = t < ntask;
-    const int item = active ? t / rq : 0, q = active ? t % rq : 0;
-    const int target = n - 1 - q;  // ascending index of the q-th largest
-    const float glo = s_lo[item], ghi = s_hi[item];
-    const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
-    const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
-    const float atol = 2.4e-7f * gnorm + 1e-30f;
-    const float alpha = (float)s_alpha[item];
-    const float* z2 = s_z2[item];
-    float a = glo, b = ghi;
-    if (sorted) {
-      if (q > 0) b = fminf(b, s_d[q - 1]);
-      if (q < rt) a = fmaxf(a, s_d[q]);
+  if (sorted) {
+    // bracketed rational-model iteration, one thread per task
+    for (int t0 = 0; t0 < ntask; t0 += kArrowThreads) {  // uniform trip count
+      const int t = t0 + tid;
+      const bool active = t < ntask;
+      const int item = active ? t / rq : 0, q = active ? t % rq : 0;
+      const float glo = s_lo[item], ghi = s_hi[item];
+      const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
+      const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
+      const float atol = 2.4e-7f * gnorm + 1e-30f;
+      const float alpha = (float)s_alpha[item];
+      const float2* dz = s_dz[item];
+      const bool has_l = q < rt, has_r = q > 0;
+      const float dl = has_l ? s_d[q] : 0.f, dr = has_r ? s_d[q - 1] : 0.f;
+      float a = has_l ? fmaxf(glo, dl) : glo, b = has_r ? fminf(ghi, dr) : ghi;
       if (a > b) a = b;
-    }
-    bool stuck = false;
-    int it = 0;
-    for (; it < kArrowBisectMax; ++it) {
-      const bool done = !active || stuck || !((b - a) > atol);
-      if (__all_sync(0xffffffffu, done)) break;
-      const float step = (b - a) / (float)(g + 1);
-      const float x = a + step * (float)(sub + 1);
-      bool above = false;
-      if (!done)
-        above = (x > a && x < b) ? (arrow_count(s_d, z2, rt, alpha, x, pivmin) > target)
-                                 : (x >= b);
-      const unsigned bal = (__ballot_sync(0xffffffffu, above) & gmask) >> shift;
-      if (!done) {
-        const int s = bal ? __ffs(bal) - 1 : g;
-        const float na = (s == 0) ? a : a + step * (float)s;
-        const float nb = (s == g) ? b : a + step * (float)(s + 1);
-        if (!(nb < b || na > a)) stuck = true;
-        a = na;
-        b = nb;
+      float x = 0.5f * (a + b), lam = x;
+      bool done = !active || !((b - a) > atol);
+      bool probed = false;
+      int it = 0;
+      for (; it < kArrowBisectMax; ++it) {
+        if (__all_sync(0xffffffffu, done)) break;
+        if (done) continue;
+        float f = alpha - x, D = 0.f;
+        for (int j = 0; j < rt; ++j) {
+          const float2 e = dz[j];
+          float qq = e.x - x;
+          if (fabsf(qq) < pivmin) qq = qq < 0.f ? -pivmin : pivmin;
+          const float inv = __fdividef(1.f, qq);
+          const float tt = e.y * inv;
+          f -= tt;
+          D = fmaf(tt, inv, D);
+        }
+        if (f < 0.f) b = x; else a = x;  // x above the root iff f(x) < 0
+        if (!((b - a) > atol)) {
+          done = true;
+          lam = x;
+          continue;
+        }
+        float delta = 0.f;
+        bool have = false;
+        if (it < kArrowModelIters && (has_l || has_r)) {
+          if (has_l && has_r) {
+            const float mid = 0.5f * (a + b);
+            const float pole = (mid - dl < dr - mid) ? dl : dr;
+            const float fp = -1.f - D;
+            const float dx = pole - x;
+            const float A = fmaf(-fp, dx, f), B = fp * dx * dx;
+            if (A != 0.f) {
+              delta = dx + B / A;
+              have = true;
+            }
+          } else {
+            const float pole = has_l ? dl : dr;
+            const float dx = pole - x;
+            const float E = D * dx * dx;
+            const float C = f + x + E / dx;
+            delta = dx + arrow_quad_root(C - pole, E, has_l);
+            have = true;
+          }
+        }
+        if (have && fabsf(delta) <= 0.5f * atol) {
+          done = true;
+          lam = x + delta;
+          continue;
+        }
+        float y = x + delta;
+        if (have && !probed && y <= a) {
+          y = a + fminf(0.5f * (b - a), 0.5f * atol);
+          probed = true;
+        } else if (have && !probed && y >= b) {
+          y = b - fminf(0.5f * (b - a), 0.5f * atol);
+          probed = true;
+        }
+        if (!have || !(y > a && y < b)) y = 0.5f * (a + b);
+        x = y;
       }
+      if (active && !done) {
+        capped = 1;
+        lam = 0.5f * (a + b);
+      }
+      if (active) s_lam[item][q] = lam;
     }
-    if (active && it == kArrowBisectMax) capped = 1;
-    if (active && sub == 0) s_lam[item][q] = 0.5f * (a + b);
+  } else {
+    // multisection bisection on the full count, g threads per task
+    int g = 1;
+    while (g < 16 && g * 2 * ntask <= kArrowThreads) g *= 2;
+    const int ngroups = kArrowThreads / g;
+    const int grp = tid / g, sub = tid % g;
+    const unsigned shift = (unsigned)((lane / g) * g);
+    const unsigned gmask = ((1u << g) - 1u) << shift;
+    for (int t0 = 0; t0 < ntask; t0 += ngroups) {  // uniform trip count across the block
+      const int t = t0 + grp;
+      const bool active = t < ntask;
+      const int item = active ? t / rq : 0, q = active ? t % rq : 0;
+      const int target = n - 1 - q;  // ascending index of the q-th largest
+      const float glo = s_lo[item], ghi = s_hi[item];
+      const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
+      const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
+      const float atol = 2.4e-7f * gnorm + 1e-30f;
+      const float alpha = (float)s_alpha[item];
+      const float* z2 = s_z2[item];
+      float a = glo, b = ghi;
+      bool stuck = false;
+      int it = 0;
+      for (; it < kArrowBisectMax; ++it) {
+        const bool done = !active || stuck || !((b - a) > atol);
+        if (__all_sync(0xffffffffu, done)) break;
+        const float step = (b - a) / (float)(g + 1);
+        const float x = a + step * (float)(sub + 1);
+        bool above = false;
+        if (!done)
+          above = (x > a && x < b) ? (arrow_count(s_d, z2, rt, alpha, x, pivmin) > target)
+                                   : (x >= b);
+        const unsigned bal = (__ballot_sync(0xffffffffu, above) & gmask) >> shift;
+        if (!done) {
+          const int s = bal ? __ffs(bal) - 1 : g;
+          const float na = (s == 0) ? a : a + step * (float)s;
+          const float nb = (s == g) ? b : a + step * (float)(s + 1);
+          if (!(nb < b || na > a)) stuck = true;
+          a = na;
+          b = nb;
+        }
+      }
+      if (active && it == kArrowBisectMax) capped = 1;
+      if (active && sub == 0) s_lam[item][q] = 0.5f * (a + b);
+    }
   }
   if (capped) atomicOr(status, kStatusBisectCap);
   __syncthreads();
@@ -255,7 +382,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
 }  // namespace
 
 // A descriptor per candidate; group = {first descriptor, count}.
-__global__ void __launch_bounds__(kArrowThreads)
+__global__ void __launch_bounds__(kArrowThreads, 7)
 core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ groups,
                   int* __restrict__ status) {
   __shared__ ArrowGroupView V;
@@ -289,7 +416,7 @@ core_arrow_kernel(const ArrowDesc* __restrict__ descs, const int2* __restrict__ 
 }
 
 // Candidates as rows of Xt; group = {first row, count, state, unused}.
-__global__ void __launch_bounds__(kArrowThreads)
+__global__ void __launch_bounds__(kArrowThreads, 7)
 core_arrow_columns_kernel(const ArrowState* __restrict__ states, const int4* __restrict__ groups,
                           const float* __restrict__ Xt, int64_t ldx, float* sigma_out,
                           int64_t ld_sigma, double* tail_out, double* paper_out,

@@ -1434,6 +1434,34 @@ std::vector<int> sorted_by(const std::vector<int>& ids, const std::vector<double
 }
 
 // Alg. 3: approximate incremental clustering.
+// First candidate of `order` (from `pos` on) whose merge with the state is
+// accepted, or order.size().  The scan is the sequential one of Alg. 3 (the
+// first candidate in order that passes joins); candidates are scored in
+// chunks of doubling size from `pos`, so an early accept does not pay for
+// scoring the whole remainder.  A candidate's score does not depend on the
+// batch it is scored in, so the decision equals that of scoring all at once.
+static csvd_status first_accept(Driver& D, csvd_state st, const std::vector<int>& order,
+                                size_t pos, size_t& hit) {
+  constexpr size_t kFirstChunk = 256;
+  const double e2 = D.eps * D.eps;
+  hit = order.size();
+  size_t chunk = kFirstChunk;
+  while (pos < order.size()) {
+    const size_t end = std::min(order.size(), pos + chunk);
+    std::vector<int> cand(order.begin() + pos, order.begin() + end);
+    std::vector<double> tail, energy;
+    CSVD_TRY(score_state(D, st, cand, tail, energy));
+    for (size_t i = 0; i < cand.size(); ++i)
+      if (tail[i] <= e2 * energy[i]) {
+        hit = pos + i;
+        return CSVD_OK;
+      }
+    pos = end;
+    chunk *= 2;
+  }
+  return CSVD_OK;
+}
+
 csvd_status cluster_approx(Driver& D, int sort_mode, std::vector<std::vector<int>>& clusters,
                            std::vector<double>& est) {
   std::vector<int> remaining(D.n);
@@ -1449,29 +1477,24 @@ csvd_status cluster_approx(Driver& D, int sort_mode, std::vector<std::vector<int
     CSVD_TRY(csvd_incr_init(&st, D.m, D.r, D.precision, D.s));
     std::vector<int> members{anchor};
     csvd_status rc = append_commit(st, &D.blocks[anchor]);
-    const double e2 = D.eps * D.eps;
     while (rc == CSVD_OK && !remaining.empty()) {
       if (sort_mode == CSVD_SORT_FROBENIUS) {
-        // one scan in ascending norm; batched scores, first accept commits
+        // one scan in ascending norm; the first accept commits, the scan
+        // goes on after it with the grown state
         std::vector<double> key(remaining.size());
         for (size_t i = 0; i < remaining.size(); ++i) key[i] = D.norms[remaining[i]];
         std::vector<int> order = sorted_by(remaining, key);
         bool any = false;
         size_t pos = 0;
         while (pos < order.size() && rc == CSVD_OK) {
-          std::vector<int> cand(order.begin() + pos, order.end());
-          std::vector<double> tail, energy;
-          rc = score_state(D, st, cand, tail, energy);
-          if (rc != CSVD_OK) break;
-          size_t hit = cand.size();
-          for (size_t i = 0; i < cand.size(); ++i)
-            if (tail[i] <= e2 * energy[i]) { hit = i; break; }
-          if (hit == cand.size()) break;
-          rc = append_commit(st, &D.blocks[cand[hit]]);
-          members.push_back(cand[hit]);
-          remaining.erase(std::find(remaining.begin(), remaining.end(), cand[hit]));
+          size_t hit = order.size();
+          rc = first_accept(D, st, order, pos, hit);
+          if (rc != CSVD_OK || hit == order.size()) break;
+          rc = append_commit(st, &D.blocks[order[hit]]);
+          members.push_back(order[hit]);
+          remaining.erase(std::find(remaining.begin(), remaining.end(), order[hit]));
           any = true;
-          pos += hit + 1;
+          pos = hit + 1;
         }
         if (!any) break;
       } else {
@@ -1479,13 +1502,9 @@ csvd_status cluster_approx(Driver& D, int sort_mode, std::vector<std::vector<int
         rc = residual_norms_state(D, st, remaining, res);
         if (rc != CSVD_OK) break;
         std::vector<int> order = sorted_by(remaining, res);
-        std::vector<double> tail, energy;
-        rc = score_state(D, st, order, tail, energy);
-        if (rc != CSVD_OK) break;
         size_t hit = order.size();
-        for (size_t i = 0; i < order.size(); ++i)
-          if (tail[i] <= e2 * energy[i]) { hit = i; break; }
-        if (hit == order.size()) break;
+        rc = first_accept(D, st, order, 0, hit);
+        if (rc != CSVD_OK || hit == order.size()) break;
         rc = append_commit(st, &D.blocks[order[hit]]);
         members.push_back(order[hit]);
         remaining.erase(std::find(remaining.begin(), remaining.end(), order[hit]));

@@ -73,12 +73,30 @@ __device__ __forceinline__ void arrow_acc_sq(float& s, float& c, float v) {
   s = t;
 }
 
+// (s, c) += (s2, c2) for double-float pairs (two-sum of the heads).
+__device__ __forceinline__ void arrow_ff_add(float& s, float& c, float s2, float c2) {
+  const float t = s + s2;
+  const float bp = t - s;
+  c += c2 + ((s - (t - bp)) + (s2 - bp));
+  s = t;
+}
+
+// Warp sum of double-float pairs; every lane gets the total.
+__device__ __forceinline__ void arrow_ff_warp_sum(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    arrow_ff_add(s, c, s2, c2);
+  }
+}
+
 // Root t of t^2 - h t - E = 0 (E >= 0): the non-negative one if `positive`,
 // else the non-positive one, each in a form free of cancellation.
 __device__ __forceinline__ float arrow_quad_root(float h, float E, bool positive) {
   const float sq = sqrtf(fmaf(h, h, 4.f * E));
-  if (positive) return h >= 0.f ? 0.5f * (h + sq) : (2.f * E) / (sq - h);
-  return h <= 0.f ? 0.5f * (h - sq) : (-2.f * E) / (sq + h);
+  if (positive) return h >= 0.f ? 0.5f * (h + sq) : __fdividef(2.f * E, sq - h);
+  return h <= 0.f ? 0.5f * (h - sq) : __fdividef(-2.f * E, sq + h);
 }
 
 // What one CTA evaluates: a state and up to kArrowGroup candidates of it.
@@ -113,7 +131,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   __shared__ float2 s_dz[kArrowGroup][kArrowMaxRt];  // {d_j, z_j^2}
   __shared__ float s_lam[kArrowGroup][kArrowMaxRt + 1];
   __shared__ float s_lo[kArrowGroup], s_hi[kArrowGroup];
-  __shared__ double s_red[kArrowWarps][kArrowGroup];
+  __shared__ float2 s_red[kArrowWarps][kArrowGroup];
   __shared__ double s_alpha[kArrowGroup];
 
   const float* ap[kArrowGroup];
@@ -169,13 +187,13 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
 #pragma unroll
   for (int g = 0; g < kArrowGroup; ++g) {
     s_part[wid][g][lane] = acc[g];
-    const double t = warp_sum_d((double)es[g] + (double)ec[g]);
-    if (lane == 0) s_red[wid][g] = t;
+    arrow_ff_warp_sum(es[g], ec[g]);
+    if (lane == 0) s_red[wid][g] = make_float2(es[g], ec[g]);
   }
   __syncthreads();
   if (tid < kArrowGroup) {
     double t = 0.0;
-    for (int w = 0; w < kArrowWarps; ++w) t += s_red[w][tid];
+    for (int w = 0; w < kArrowWarps; ++w) t += (double)s_red[w][tid].x + (double)s_red[w][tid].y;
     s_alpha[tid] = t;
   }
   bool sorted_ok = true;
@@ -247,8 +265,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
         float f = alpha - x, D = 0.f;
         for (int j = 0; j < rt; ++j) {
           const float2 e = dz[j];
-          float qq = e.x - x;
-          if (fabsf(qq) < pivmin) qq = qq < 0.f ? -pivmin : pivmin;
+          const float qq = copysignf(fmaxf(fabsf(e.x - x), pivmin), e.x - x);
           const float inv = __fdividef(1.f, qq);
           const float tt = e.y * inv;
           f -= tt;
@@ -270,14 +287,14 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
             const float dx = pole - x;
             const float A = fmaf(-fp, dx, f), B = fp * dx * dx;
             if (A != 0.f) {
-              delta = dx + B / A;
+              delta = dx + __fdividef(B, A);
               have = true;
             }
           } else {
             const float pole = has_l ? dl : dr;
             const float dx = pole - x;
             const float E = D * dx * dx;
-            const float C = f + x + E / dx;
+            const float C = f + x + __fdividef(E, dx);
             delta = dx + arrow_quad_root(C - pole, E, has_l);
             have = true;
           }
@@ -357,15 +374,17 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   if (wid < cnt) {
     const double alpha_d = s_alpha[wid];
     float* sig_out = V.sigma_out[wid];
-    double top = 0.0, tr = 0.0;
+    float ts = 0.f, tc = 0.f, ds = 0.f, dc = 0.f;  // double-float sums of the top and of d
     for (int q = lane; q < rq; q += 32) {
-      top += (double)s_lam[wid][q];
+      arrow_ff_add(ts, tc, s_lam[wid][q], 0.f);
       sig_out[q] = sqrtf(fmaxf(s_lam[wid][q], 0.f));
     }
-    for (int j = lane; j < rt; j += 32) tr += (double)s_d[j];
-    top = warp_sum_d(top);
-    tr = warp_sum_d(tr) + alpha_d;
+    for (int j = lane; j < rt; j += 32) arrow_ff_add(ds, dc, s_d[j], 0.f);
+    arrow_ff_warp_sum(ts, tc);
+    arrow_ff_warp_sum(ds, dc);
     if (lane == 0) {
+      const double top = (double)ts + (double)tc;
+      const double tr = (double)ds + (double)dc + alpha_d;
       const double energy_new = V.scal[0] + alpha_d;
       double tail = V.scal[1] + (tr - top);
       if (tail < 0.0) tail = 0.0;

@@ -150,7 +150,14 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   const int slab = nslab > 0 ? wid % nslab : 0, rg = nslab > 0 ? wid / nslab : wid;
   const int col = slab * 32 + lane;
   const bool pj_on = nslab > 0 && rg < nrg && col < rt;
-  float acc[kArrowGroup] = {};
+  // 16-byte rows of U: a lane reads 4 columns at once (lane % 8 picks the
+  // column quad of the slab, lane / 8 the row within a block of 4 rows;
+  // blocks of 4 rows go round-robin to the row groups) and keeps 4 x 4
+  // sums; otherwise a lane reads one column and keeps acc[g][0]
+  const bool vec = (ldu & 3) == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
+  const int quad = lane & 7, rsub = lane >> 3;
+  const bool quad_on = nslab > 0 && rg < nrg && slab * 32 + 4 * quad < rt;
+  float acc[kArrowGroup][4] = {};
   float es[kArrowGroup] = {}, ec[kArrowGroup] = {};
   for (int64_t i0 = 0; i0 < m; i0 += kArrowStage) {
     const int len = (int)(m - i0 < kArrowStage ? m - i0 : kArrowStage);
@@ -170,23 +177,54 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
       for (int g = 0; g < kArrowGroup; ++g) arrow_acc_sq(es[g], ec[g], v[k][g]);
     }
     __syncthreads();
-    if (pj_on) {
+    if (vec) {
+      if (quad_on) {
+        const float* u = U + i0 * ldu + slab * 32 + 4 * quad;
+#pragma unroll 4
+        for (int ii = 4 * rg + rsub; ii < len; ii += 4 * nrg) {
+          const float4 uu = __ldg(reinterpret_cast<const float4*>(u + (int64_t)ii * ldu));
+          const float4 x = s_a[ii];
+          const float xs[kArrowGroup] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int g = 0; g < kArrowGroup; ++g) {
+            acc[g][0] = fmaf(uu.x, xs[g], acc[g][0]);
+            acc[g][1] = fmaf(uu.y, xs[g], acc[g][1]);
+            acc[g][2] = fmaf(uu.z, xs[g], acc[g][2]);
+            acc[g][3] = fmaf(uu.w, xs[g], acc[g][3]);
+          }
+        }
+      }
+    } else if (pj_on) {
       const float* u = U + i0 * ldu + col;
 #pragma unroll 16
       for (int ii = rg; ii < len; ii += nrg) {
         const float uu = __ldg(u + (int64_t)ii * ldu);
         const float4 x = s_a[ii];
-        acc[0] = fmaf(uu, x.x, acc[0]);
-        acc[1] = fmaf(uu, x.y, acc[1]);
-        acc[2] = fmaf(uu, x.z, acc[2]);
-        acc[3] = fmaf(uu, x.w, acc[3]);
+        acc[0][0] = fmaf(uu, x.x, acc[0][0]);
+        acc[1][0] = fmaf(uu, x.y, acc[1][0]);
+        acc[2][0] = fmaf(uu, x.z, acc[2][0]);
+        acc[3][0] = fmaf(uu, x.w, acc[3][0]);
       }
     }
     __syncthreads();
   }
+  if (vec) {  // sum the 4 row lanes of each column quad
+#pragma unroll
+    for (int g = 0; g < kArrowGroup; ++g)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        acc[g][c] += __shfl_xor_sync(0xffffffffu, acc[g][c], 8);
+        acc[g][c] += __shfl_xor_sync(0xffffffffu, acc[g][c], 16);
+      }
+  }
 #pragma unroll
   for (int g = 0; g < kArrowGroup; ++g) {
-    s_part[wid][g][lane] = acc[g];
+    if (!vec) {
+      s_part[wid][g][lane] = acc[g][0];
+    } else if (rsub == 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s_part[wid][g][4 * quad + c] = acc[g][c];
+    }
     arrow_ff_warp_sum(es[g], ec[g]);
     if (lane == 0) s_red[wid][g] = make_float2(es[g], ec[g]);
   }

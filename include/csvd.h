@@ -155,6 +155,42 @@ csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
                                double eps, float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
                                double* tail_paper_out, uint8_t* accept_out);
 
+/* Streaming cluster assignment: the incremental setting named as future
+ * work in the paper's discussion section, where matrices arrive one at a
+ * time and each joins an existing cluster or starts a new one by its
+ * predicted compression error.  The rule (the paper gives none): a pushed
+ * block is scored against every open cluster in one batched evaluation
+ * (csvd_score semantics: a tentative rank-r append, Lemma 1 and Cor. 3, and
+ * the plug-in estimate of Cor. 2); a cluster accepts when
+ * E~^2 <= eps^2 ||M_{C u block}||_F^2; among the accepting clusters the one
+ * with the smallest E~^2 / ||M||_F^2 receives the block (ties to the lowest
+ * index) and commits it; when none accepts, the block starts a new cluster.
+ * Clusters are numbered in order of creation.  The stream owns its cluster
+ * states; precision as in csvd_incr_init; stream-ordered work on
+ * cuda_stream.  Errors: CSVD_ERR_ARG for bad sizes, eps < 0 or a bad
+ * precision. */
+typedef struct csvd_stream_s* csvd_stream;
+csvd_status csvd_stream_init(csvd_stream* out, int64_t m, int32_t r, double eps,
+                             int32_t precision, void* cuda_stream);
+
+/* Assign one block (m x k, borrowed for the call).  Host outputs, any may be
+ * NULL: the cluster index, and E~^2 (accumulated discarded energy) and
+ * ||M_C||_F^2 of that cluster after the block joined.  Syncs. */
+csvd_status csvd_stream_push(csvd_stream s, const csvd_block* block, int32_t* label_out,
+                             double* tail_sq_out, double* energy_out);
+
+/* Number of clusters so far. */
+csvd_status csvd_stream_count(csvd_stream s, int32_t* n_clusters);
+
+/* Cluster c's state (borrowed: valid until csvd_stream_free; read it with
+ * csvd_incr_sigma / csvd_incr_basis / csvd_tail_error to export the
+ * cluster's basis) and its number of blocks (either output may be NULL). */
+csvd_status csvd_stream_cluster(csvd_stream s, int32_t c, csvd_state* state_out,
+                                int32_t* n_blocks_out);
+
+/* Release the stream and every cluster state it owns. */
+csvd_status csvd_stream_free(csvd_stream s);
+
 /* Bounds for blocks taken in the given order (Section 3):
  *   weyl_sq     Thm. 1: sum ||A_j||^2 - max_j sum_{i<=r} sigma_i^2(A_j)
  *   residual_sq Cor. 1: sum ||A_j||^2 - sum_{j<=r} mu_j^2, mu the singular

@@ -1049,6 +1049,136 @@ csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
   return CSVD_OK;
 }
 
+// ------------------------------------------------ streaming assignment
+}  // extern "C"
+
+struct csvd_stream_s {
+  int64_t m = 0;
+  int r = 0;
+  double eps = 0.0;
+  int prec = 0;
+  cudaStream_t s = nullptr;
+  std::vector<csvd_state> clusters;
+  std::vector<int32_t> sizes;  // blocks per cluster
+};
+
+extern "C" {
+
+csvd_status csvd_stream_init(csvd_stream* out, int64_t m, int32_t r, double eps,
+                             int32_t precision, void* cuda_stream) {
+  if (!out) return fail(CSVD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || m > 65536 || r < 1 || r > 1024 || r > m)
+    return fail(CSVD_ERR_ARG, "need 1 <= r <= min(m, 1024), m <= 65536");
+  if (!(eps >= 0.0)) return fail(CSVD_ERR_ARG, "need eps >= 0");
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+    return fail(CSVD_ERR_ARG, "bad precision");
+  csvd_stream_s* h = new csvd_stream_s();
+  h->m = m;
+  h->r = r;
+  h->eps = eps;
+  h->prec = precision;
+  h->s = static_cast<cudaStream_t>(cuda_stream);
+  *out = h;
+  return CSVD_OK;
+}
+
+csvd_status csvd_stream_push(csvd_stream h, const csvd_block* block, int32_t* label_out,
+                             double* tail_sq_out, double* energy_out) {
+  if (!h || !block) return fail(CSVD_ERR_ARG, "NULL argument");
+  CSVD_TRY(check_block(block, h->m));
+  const int C = (int)h->clusters.size();
+  int best = -1;
+  if (C > 0) {
+    // one batched evaluation of the block against every open cluster
+    Layout L;
+    const size_t o_sig = L.add(sizeof(float) * (size_t)C * h->r);
+    const size_t o_t = L.add(sizeof(double) * C);
+    const size_t o_e = L.add(sizeof(double) * C);
+    Workspace w;
+    w.s = h->s;
+    w.base = static_cast<char*>(dev_alloc(L.size, h->s));
+    if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+    std::vector<Item> items(C);
+    for (int c = 0; c < C; ++c)
+      items[c] = Item{view_of(h->clusters[c]), block, h->r, h->m,
+                      w.at<float>(o_sig) + (size_t)c * h->r, w.at<double>(o_t) + c, nullptr,
+                      w.at<double>(o_e) + c, nullptr};
+    int* d_status = h->clusters[0]->status;
+    {
+      Workspace ws;
+      CSVD_TRY(run_items(items, h->eps, h->prec, h->s, d_status, ws, nullptr, false));
+    }
+    std::vector<double> tail(C), energy(C);
+    CUDA_TRY(cudaMemcpyAsync(tail.data(), w.base + o_t, sizeof(double) * C, cudaMemcpyDeviceToHost,
+                             h->s));
+    CUDA_TRY(cudaMemcpyAsync(energy.data(), w.base + o_e, sizeof(double) * C,
+                             cudaMemcpyDeviceToHost, h->s));
+    CSVD_TRY(take_status(d_status, h->s));
+    // best fit: the smallest estimated relative error among the clusters
+    // that accept (ties to the lowest index)
+    const double e2 = h->eps * h->eps;
+    double best_rel = 0.0;
+    for (int c = 0; c < C; ++c) {
+      if (!(tail[c] <= e2 * energy[c])) continue;
+      const double rel = energy[c] > 0.0 ? tail[c] / energy[c] : 0.0;
+      if (best < 0 || rel < best_rel) {
+        best = c;
+        best_rel = rel;
+      }
+    }
+  }
+  if (best < 0) {
+    csvd_state st = nullptr;
+    CSVD_TRY(csvd_incr_init(&st, h->m, h->r, h->prec, h->s));
+    const csvd_status rc = append_commit(st, block);
+    if (rc != CSVD_OK) {
+      csvd_incr_free(st);
+      return rc;
+    }
+    h->clusters.push_back(st);
+    h->sizes.push_back(1);
+    best = C;
+  } else {
+    CSVD_TRY(append_commit(h->clusters[best], block));
+    h->sizes[best] += 1;
+  }
+  if (label_out) *label_out = best;
+  if (tail_sq_out || energy_out) {
+    double t = 0.0, en = 0.0;
+    CSVD_TRY(csvd_tail_error(h->clusters[best], &t, nullptr, nullptr, &en));
+    if (tail_sq_out) *tail_sq_out = t;
+    if (energy_out) *energy_out = en;
+  }
+  return CSVD_OK;
+}
+
+csvd_status csvd_stream_count(csvd_stream h, int32_t* n_clusters) {
+  if (!h || !n_clusters) return fail(CSVD_ERR_ARG, "NULL argument");
+  *n_clusters = (int32_t)h->clusters.size();
+  return CSVD_OK;
+}
+
+csvd_status csvd_stream_cluster(csvd_stream h, int32_t c, csvd_state* state_out,
+                                int32_t* n_blocks_out) {
+  if (!h) return fail(CSVD_ERR_ARG, "NULL argument");
+  if (c < 0 || c >= (int32_t)h->clusters.size()) return fail(CSVD_ERR_ARG, "no such cluster");
+  if (state_out) *state_out = h->clusters[c];
+  if (n_blocks_out) *n_blocks_out = h->sizes[c];
+  return CSVD_OK;
+}
+
+csvd_status csvd_stream_free(csvd_stream h) {
+  if (!h) return CSVD_OK;
+  csvd_status rc = CSVD_OK;
+  for (csvd_state st : h->clusters) {
+    const csvd_status r2 = csvd_incr_free(st);
+    if (rc == CSVD_OK) rc = r2;
+  }
+  delete h;
+  return rc;
+}
+
 }  // extern "C"
 
 // ====================================================== internal helpers

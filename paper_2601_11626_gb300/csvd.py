@@ -64,6 +64,11 @@ def _sig(lib):
     lib.csvd_incr_free.argtypes = [VP]
     lib.csvd_score.argtypes = [P(VP), I32, P(I32), P(Block), I32, D, I32, VP, I64, VP, VP, VP]
     lib.csvd_score_columns.argtypes = [P(VP), I32, P(I32), VP, I64, I32, D, VP, I64, VP, VP, VP]
+    lib.csvd_stream_init.argtypes = [P(VP), I64, I32, D, I32, VP]
+    lib.csvd_stream_push.argtypes = [VP, P(Block), P(I32), P(D), P(D)]
+    lib.csvd_stream_count.argtypes = [VP, P(I32)]
+    lib.csvd_stream_cluster.argtypes = [VP, I32, P(VP), P(I32)]
+    lib.csvd_stream_free.argtypes = [VP]
     lib.csvd_bounds.argtypes = [P(Block), I32, I64, I32, VP, P(D), P(D), P(D), P(D)]
     lib.csvd_cluster.argtypes = [P(Block), I32, I64, I32, D, I32, I32, I32, VP, P(I32), P(D),
                                  P(D), P(D)]
@@ -80,6 +85,8 @@ def _sig(lib):
     for name in ("csvd_incr_init", "csvd_incr_append", "csvd_incr_sigma", "csvd_incr_basis",
                  "csvd_incr_load", "csvd_gram_apply",
                  "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_score_columns", "csvd_bounds",
+                 "csvd_stream_init", "csvd_stream_push", "csvd_stream_count",
+                 "csvd_stream_cluster", "csvd_stream_free",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator"):
         getattr(lib, name).restype = C.c_int
 
@@ -113,11 +120,16 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
-def block(t: torch.Tensor) -> Block:
+def block(t: torch.Tensor, m: int = None) -> Block:
     """Descriptor of a row-major (m, k) CUDA tensor (f32 or bf16, unit
-    column stride)."""
-    if not t.is_cuda or t.dim() != 2:
-        raise ValueError("blocks must be 2-D CUDA tensors")
+    column stride).  The C ABI reads m rows from the pointer, so the row
+    count is checked here whenever m is known."""
+    if t.dim() != 2:
+        raise ValueError("blocks must be 2-D tensors")
+    if m is not None and t.shape[0] != m:
+        raise ValueError(f"block has {t.shape[0]} rows, expected m = {m}")
+    if not t.is_cuda:
+        raise ValueError("blocks must be CUDA tensors")
     if t.stride(1) != 1 and t.shape[1] > 1:
         raise ValueError("blocks need unit column stride (row-major)")
     if t.dtype == torch.float32:
@@ -130,10 +142,14 @@ def block(t: torch.Tensor) -> Block:
     return Block(t.data_ptr(), t.shape[1], max(ld, t.shape[1]), dt, 0)
 
 
-def _blocks(ts):
+def _blocks(ts, m: int = None):
+    """Descriptor array; every block must have m rows (default: the first
+    block's row count)."""
+    if m is None and len(ts) > 0:
+        m = ts[0].shape[0]
     arr = (Block * len(ts))()
     for i, t in enumerate(ts):
-        arr[i] = block(t)
+        arr[i] = block(t, m)
     return arr
 
 
@@ -151,7 +167,7 @@ class IncrSVD:
         self._keep = []
 
     def append(self, A: torch.Tensor):
-        b = block(A)
+        b = block(A, self.m)
         _check(self._lib.csvd_incr_append(self._h, C.byref(b)))
         self._keep.append(A)  # borrowed until the stream reaches it
         if len(self._keep) > 64:
@@ -221,6 +237,71 @@ class IncrSVD:
             pass
 
 
+class _BorrowedState(IncrSVD):
+    """A cluster state owned by a Stream (read-only view: sigma, basis,
+    tail_error, decompose); released with the stream."""
+
+    def __init__(self, lib_, handle, m, r, stream):
+        self._lib, self._h, self.m, self.r, self.stream = lib_, handle, m, r, stream
+        self._keep = []
+
+    def append(self, A):
+        raise RuntimeError("a stream's cluster states change only through Stream.push")
+
+    def close(self):
+        self._h = None
+
+
+class Stream:
+    """Streaming cluster assignment (csvd_stream_*): each pushed block joins
+    the accepting cluster with the smallest estimated relative error, or
+    starts a new cluster."""
+
+    def __init__(self, m: int, r: int, eps: float, precision: str = "mixed", stream=None):
+        self._lib = lib()
+        self.m, self.r, self.eps = m, r, float(eps)
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(self._lib.csvd_stream_init(C.byref(h), m, r, self.eps,
+                                          MIXED if precision == "mixed" else PLAIN,
+                                          _stream(self.stream)))
+        self._h = h
+        self.labels = []
+
+    def push(self, A: torch.Tensor):
+        """Returns (cluster index, E~^2 and ||M_C||^2 of that cluster after
+        the block joined)."""
+        b = block(A, self.m)
+        lab, t, en = C.c_int32(), C.c_double(), C.c_double()
+        _check(self._lib.csvd_stream_push(self._h, C.byref(b), C.byref(lab), C.byref(t),
+                                          C.byref(en)))
+        self.labels.append(lab.value)
+        return lab.value, t.value, en.value
+
+    @property
+    def n_clusters(self) -> int:
+        n = C.c_int32()
+        _check(self._lib.csvd_stream_count(self._h, C.byref(n)))
+        return n.value
+
+    def cluster(self, c: int):
+        """(state view, number of blocks) of cluster c."""
+        h, nb = C.c_void_p(), C.c_int32()
+        _check(self._lib.csvd_stream_cluster(self._h, c, C.byref(h), C.byref(nb)))
+        return _BorrowedState(self._lib, h, self.m, self.r, self.stream), nb.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.csvd_stream_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class ScoreBatch:
     """Prepared descriptor arrays for repeated ``csvd_score`` calls on the
     same candidates (avoids rebuilding ctypes arrays inside timed loops)."""
@@ -233,7 +314,7 @@ class ScoreBatch:
         self.precision = MIXED if precision == "mixed" else PLAIN
         self._st = (C.c_void_p * len(states))(*[s.handle.value for s in states])
         self._cs = (C.c_int32 * self.n)(*[int(x) for x in cand_state])
-        self._cb = _blocks(cands)
+        self._cb = _blocks(cands, states[0].m)
         self.cands = cands
         self.r_max = r_max or max(s.r for s in states)
         self.sigma = torch.zeros(self.n, self.r_max, device="cuda", dtype=torch.float32)
@@ -259,6 +340,8 @@ class ScoreColumns:
     def __init__(self, states, cand_state, Xt, eps, r_max=None):
         if Xt.dtype != torch.float32 or not Xt.is_cuda or Xt.dim() != 2 or Xt.stride(1) != 1:
             raise ValueError("Xt must be a CUDA float32 matrix with unit column stride")
+        if Xt.shape[1] != states[0].m:
+            raise ValueError(f"Xt rows have {Xt.shape[1]} entries, expected m = {states[0].m}")
         self._lib = lib()
         self.states = states
         self.Xt = Xt
@@ -310,7 +393,7 @@ def score_one_noalloc(state: IncrSVD, A: torch.Tensor, eps: float, sigma=None, t
         paper = torch.zeros(1, device="cuda", dtype=torch.float64)
     if accept is None:
         accept = torch.zeros(1, device="cuda", dtype=torch.uint8)
-    b = block(A)
+    b = block(A, state.m)
     _check(lib().csvd_score_one_noalloc(state.handle, C.byref(b), float(eps),
                                         C.c_void_p(sigma.data_ptr()), C.c_void_p(tail.data_ptr()),
                                         C.c_void_p(paper.data_ptr()),
@@ -357,6 +440,8 @@ def cluster(blocks, r, eps, algo="approx", sort_mode="frobenius", precision="pla
 def tail_grad(U: torch.Tensor, blocks, g: float = 1.0):
     """dA_j = 2 g (I - U U^T) A_j for every block (new f32 tensors)."""
     m = blocks[0].shape[0]
+    if U.shape[0] != m:
+        raise ValueError(f"U has {U.shape[0]} rows, the blocks {m}")
     grads = [torch.empty_like(b, dtype=torch.float32) for b in blocks]
     U = U.contiguous() if U.stride(1) != 1 else U
     _check(lib().csvd_tail_grad(C.c_void_p(U.data_ptr()), U.stride(0), m, U.shape[1],
@@ -399,7 +484,7 @@ def reconstruct(U: torch.Tensor, s, blocks, want_v: bool = True) -> Decompositio
     res = (C.c_double * max(n, 1))()
     en = (C.c_double * max(n, 1))()
     _check(lib().csvd_reconstruct(C.c_void_p(U.data_ptr()), U.stride(0), C.c_void_p(sd.data_ptr()), m,
-                                  r, _blocks(blocks), n, C.c_void_p(Ut.data_ptr()), r, vptr, r,
+                                  r, _blocks(blocks, m), n, C.c_void_p(Ut.data_ptr()), r, vptr, r,
                                   _stream(), res, en))
     return Decomposition(Ut, V, np.array(res[:n], dtype=np.float64),
                          np.array(en[:n], dtype=np.float64))
@@ -410,7 +495,7 @@ def gram_apply(U: torch.Tensor, blocks) -> torch.Tensor:
     m, r = U.shape
     U = U.contiguous()
     Y = torch.empty(m, r, device="cuda", dtype=torch.float32)
-    _check(lib().csvd_gram_apply(C.c_void_p(U.data_ptr()), U.stride(0), m, r, _blocks(blocks),
+    _check(lib().csvd_gram_apply(C.c_void_p(U.data_ptr()), U.stride(0), m, r, _blocks(blocks, m),
                                  len(blocks), C.c_void_p(Y.data_ptr()), Y.stride(0), _stream()))
     return Y
 

@@ -76,3 +76,15 @@ def test_product_path_does_not_import_oracle():
 
 def test_build_flags_target_sm103a_only():
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_checks_row_counts_before_any_call():
+    """The C ABI reads m rows from a block pointer; the binding refuses a
+    block with a different row count before anything reaches the library
+    (checked on CPU tensors, where the device test comes first)."""
+    from paper_2601_11626_gb300 import csvd
+    import torch
+    with pytest.raises(ValueError, match="rows, expected m = 8"):
+        csvd.block(torch.zeros(7, 2), 8)
+    with pytest.raises(ValueError, match="rows, expected m = 8"):
+        csvd._blocks([torch.zeros(7, 2), torch.zeros(8, 2)], 8)

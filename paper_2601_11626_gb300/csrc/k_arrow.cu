@@ -6,16 +6,16 @@
 // whose eigenvalues are the squared singular values of the merge.  For x off
 // the poles d_j, G - xI has as many negative eigenvalues as diag(d) - xI
 // plus the sign of its Schur complement, so
-//     #{lambda < x} = #{j : d_j < x} + [alpha - x - sum_j z_j^2 / (d_j - x) < 0],
-// an exact O(r_t) count.  Multisection bisection on it gives the top r_new
-// eigenvalues (sigma~_j = sqrt(lambda_j), Cor. 3) and the tail follows from
-// the trace, tr(G) - sum of the top, in FP64.
+//     #{lambda < x} = #{j : d_j < x} + [f(x) < 0],
+//     f(x) = alpha - x - sum_j z_j^2 / (d_j - x)   (the secular function),
+// an exact O(r_t) count.  The top r_new eigenvalues give sigma~_j =
+// sqrt(lambda_j) (Cor. 3) and the tail follows from the trace, tr(G) - sum
+// of the top, summed as double-float pairs and finished in FP64.
 //
 // diag(d) is the leading principal block of G, so (Cauchy interlacing) with
 // s non-increasing the q-th largest eigenvalue lies in [d_q, d_{q-1}] (ends
 // closed by the Gershgorin interval).  Inside that bracket no pole lies
-// between x and the root, the count is (r_t - q) + [f(x) < 0] with the
-// secular function f(x) = alpha - x - sum_j z_j^2 / (d_j - x), and f is
+// between x and the root, the count is (r_t - q) + [f(x) < 0], and f is
 // decreasing; each evaluation narrows the bracket by the sign of f and
 // proposes the next point from a rational model fitted to f and f' at x:
 //   interior brackets: one pole (the end nearer the bracket's centre),
@@ -25,16 +25,17 @@
 // A proposal outside the bracket is replaced by the midpoint; once proposals
 // have run kArrowModelIters times the rest is plain bisection, so every
 // eigenvalue ends within 16 + 24 evaluations.  States whose sigma is not
-// sorted fall back to multisection bisection on the full inertia count over
-// the Gershgorin interval.
+// sorted fall back to multisection bisection on the full count over the
+// Gershgorin interval.
 //
 // One 128-thread CTA per group of up to kArrowGroup candidates of the same
-// state: rows of the group's columns are staged in shared memory up to 1024
-// at a time (all loads of a pass in flight together) and every row of U read
-// from L2 serves the whole group.  ||a||^2 is accumulated per thread as a
-// compensated FP32 pair and only the per-thread totals are added in FP64.  Two entry
-// kernels fill the group's view (a descriptor per candidate, or candidates
-// as the rows of one matrix with outputs indexed by row) and share the body.
+// state.  The group's columns are staged in shared memory 512 rows at a time
+// (all loads of a pass in flight together), so every row of U read from L2
+// serves the whole group; with 16-byte rows of U a lane reads 4 columns at
+// once.  ||a||^2 is accumulated per thread as a compensated FP32 pair.  Two
+// entry kernels fill the group's view (a descriptor per candidate, or
+// candidates as the rows of one matrix with outputs indexed by row) and
+// share the body.
 #include "common.cuh"
 
 namespace csvd {
@@ -142,8 +143,8 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
     lda[g] = g < cnt ? V.lda[g] : 0;
   }
 
-  // 1. p = U^T a for every candidate and ||a||^2 (FP64 totals).  The r_t
-  //    columns of U are cut into 32-wide slabs, one per warp; warps left
+  // 1. p = U^T a for every candidate and ||a||^2 (double-float pairs).  The
+  //    r_t columns of U are cut into 32-wide slabs, one per warp; warps left
   //    over split the rows of each staged chunk between them.
   const int nslab = (rt + 31) / 32;
   const int nrg = nslab > 0 ? kArrowWarps / nslab : 1;

@@ -687,6 +687,12 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g, cd_m;
   std::vector<TcItem> tci; std::vector<TcTile> tct;
   build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g, cd_m, tci, tct);
+  if (mixed) {
+    // one CTA per core, dispatched in descriptor order: the largest cores
+    // (cost ~ n^3) first, so the end of each launch is not one big core
+    auto larger = [](const CoreDesc& a, const CoreDesc& b) { return a.rt + a.k > b.rt + b.k; };
+    for (auto* v : {&cd_s, &cd_m, &cd_g}) std::stable_sort(v->begin(), v->end(), larger);
+  }
   const size_t o_ed = pk.add(ed), o_qd = pk.add(qd), o_cs = pk.add(cd_s), o_cg = pk.add(cd_g);
   const size_t o_cm = pk.add(cd_m);
   const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);

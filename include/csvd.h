@@ -191,6 +191,15 @@ csvd_status csvd_stream_cluster(csvd_stream s, int32_t c, csvd_state* state_out,
 /* Release the stream and every cluster state it owns. */
 csvd_status csvd_stream_free(csvd_stream s);
 
+/* Host-side consistency checks of the library's launch planning, no GPU
+ * needed: the tile placement of the eigen core for every launch class and
+ * core size (tiles partitioned among global memory, shared memory and
+ * TMEM within their capacities), its tile-list walk, the launch classes'
+ * shared memory, and the row grouping of csvd_score_columns.  Writes "ok"
+ * or the first failure into msg (cap bytes, may be NULL); returns CSVD_OK
+ * or CSVD_ERR_SHAPE. */
+csvd_status csvd_selftest(char* msg, int64_t cap);
+
 /* Bounds for blocks taken in the given order (Section 3):
  *   weyl_sq     Thm. 1: sum ||A_j||^2 - max_j sum_{i<=r} sigma_i^2(A_j)
  *   residual_sq Cor. 1: sum ||A_j||^2 - sum_{j<=r} mu_j^2, mu the singular

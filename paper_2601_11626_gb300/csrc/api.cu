@@ -983,6 +983,33 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
   return run_items(items, eps, precision, s, states[0]->status, ws, nullptr, false);
 }
 
+}  // extern "C"
+
+// Rows of csvd_score_columns in CTA groups {first row, count, state, 0}: runs
+// of adjacent rows of one state, at most kArrowGroup each; rows whose state
+// cannot take the one-column core go to `rest` in order.
+static csvd_status arrow_row_groups(const int32_t* cand_state, int n, int n_states,
+                                    const std::vector<char>& arrow_ok, std::vector<int4>& groups,
+                                    std::vector<int>& rest) {
+  groups.clear();
+  rest.clear();
+  for (int j = 0; j < n; ++j) {
+    const int si = cand_state ? cand_state[j] : 0;
+    if (si < 0 || si >= n_states) return fail(CSVD_ERR_ARG, "bad cand_state");
+    if (!arrow_ok[si]) {
+      rest.push_back(j);
+      continue;
+    }
+    if (groups.empty() || groups.back().z != si || groups.back().y == kArrowGroup ||
+        groups.back().x + groups.back().y != j)
+      groups.push_back(make_int4(j, 0, si, 0));
+    ++groups.back().y;
+  }
+  return CSVD_OK;
+}
+
+extern "C" {
+
 csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
                                const int32_t* cand_state, const float* Xt, int64_t ldx, int32_t n,
                                double eps, float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
@@ -1007,22 +1034,13 @@ csvd_status csvd_score_columns(const csvd_state* states, int32_t n_states,
   // runs of adjacent rows of one state, up to kArrowGroup per CTA; rows of
   // states past the one-column core's limit take the general path
   std::vector<int4> groups;
-  std::vector<csvd_block> rest_blocks;
   std::vector<int> rest_rows;
-  for (int j = 0; j < n; ++j) {
-    const int si = cand_state ? cand_state[j] : 0;
-    if (si < 0 || si >= n_states) return fail(CSVD_ERR_ARG, "bad cand_state");
-    if (ld_sigma < states[si]->r) return fail(CSVD_ERR_ARG, "ld_sigma < r");
-    if (!arrow_ok[si]) {
-      rest_blocks.push_back(csvd_block{Xt + (int64_t)j * ldx, 1, 1, CSVD_F32, 0});
-      rest_rows.push_back(j);
-      continue;
-    }
-    if (groups.empty() || groups.back().z != si || groups.back().y == kArrowGroup ||
-        groups.back().x + groups.back().y != j)
-      groups.push_back(make_int4(j, 0, si, 0));
-    ++groups.back().y;
-  }
+  CSVD_TRY(arrow_row_groups(cand_state, n, n_states, arrow_ok, groups, rest_rows));
+  for (int j = 0; j < n; ++j)
+    if (ld_sigma < states[cand_state ? cand_state[j] : 0]->r)
+      return fail(CSVD_ERR_ARG, "ld_sigma < r");
+  std::vector<csvd_block> rest_blocks;
+  for (int j : rest_rows) rest_blocks.push_back(csvd_block{Xt + (int64_t)j * ldx, 1, 1, CSVD_F32, 0});
   if (!groups.empty()) {
     const size_t tab_bytes = sizeof(ArrowState) * n_states, grp_bytes = sizeof(int4) * groups.size();
     const size_t grp_off = (tab_bytes + 15) & ~size_t(15);
@@ -1172,6 +1190,52 @@ csvd_status csvd_stream_cluster(csvd_stream h, int32_t c, csvd_state* state_out,
   if (state_out) *state_out = h->clusters[c];
   if (n_blocks_out) *n_blocks_out = h->sizes[c];
   return CSVD_OK;
+}
+
+csvd_status csvd_selftest(char* msg, int64_t cap) {
+  std::string err = tridiag_selftest();
+  if (err.empty()) {
+    // candidate grouping of csvd_score_columns on pseudo-random patterns
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    auto next = [&x](int mod) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      return (int)(x % (uint64_t)mod);
+    };
+    for (int trial = 0; trial < 500 && err.empty(); ++trial) {
+      const int n = 1 + next(200), n_states = 1 + next(6);
+      std::vector<char> ok(n_states);
+      for (auto& o : ok) o = next(4) != 0;
+      std::vector<int32_t> cs(n);
+      for (int j = 0; j < n; ++j) cs[j] = (j > 0 && next(3) != 0) ? cs[j - 1] : next(n_states);
+      std::vector<int4> groups;
+      std::vector<int> rest;
+      if (arrow_row_groups(cs.data(), n, n_states, ok, groups, rest) != CSVD_OK) {
+        err = "row grouping rejected a valid pattern";
+        break;
+      }
+      std::vector<int> seen(n, 0);
+      for (const int4& g : groups) {
+        if (g.y < 1 || g.y > kArrowGroup || !ok[g.z]) err = "row group size or state";
+        for (int t = 0; t < g.y && err.empty(); ++t) {
+          if (g.x + t >= n || cs[g.x + t] != g.z) err = "row group not one state";
+          else ++seen[g.x + t];
+        }
+      }
+      for (int j : rest) {
+        if (ok[cs[j]]) err = "row sent to the general path needlessly";
+        ++seen[j];
+      }
+      for (int j = 0; j < n && err.empty(); ++j)
+        if (seen[j] != 1) err = "row not covered exactly once";
+    }
+  }
+  if (msg && cap > 0) {
+    std::strncpy(msg, err.empty() ? "ok" : err.c_str(), (size_t)cap - 1);
+    msg[cap - 1] = 0;
+  }
+  return err.empty() ? CSVD_OK : fail(CSVD_ERR_SHAPE, err.c_str());
 }
 
 csvd_status csvd_stream_free(csvd_stream h) {

@@ -4,6 +4,8 @@
 // and ranks (the uneven batches of batched merge scoring).
 #pragma once
 
+#include <string>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -199,6 +201,7 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
                                int* d_status, cudaStream_t s);
 cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
                                 int* d_status, cudaStream_t s);
+std::string tridiag_selftest();
 cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
                               int* d_status, cudaStream_t s);
 // Candidates as rows of one matrix: group g = {first row, count, state, 0};

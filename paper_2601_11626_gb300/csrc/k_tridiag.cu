@@ -40,6 +40,9 @@
 //  4. FP64 epilogue: sigma~, tail = discarded_state + tr(T) - sum top, the
 //     subtraction form sum ||A||^2 - sum sigma~^2, and the accept flag; the
 //     block energy ||A||^2 is the trace of A^T A unless given.
+#include <cstdio>
+#include <string>
+
 #include "common.cuh"
 #include "tmem.cuh"
 
@@ -94,7 +97,7 @@ __host__ __device__ TileLayout tile_layout(int n, int tmem_cols, int smem_bytes,
 }
 
 // List position L -> tile (a, b) (rows a >= b).
-__device__ __forceinline__ void tile_of(int L, int T, int& a, int& b) {
+__host__ __device__ __forceinline__ void tile_of(int L, int T, int& a, int& b) {
   const float q = (float)(2 * T + 1);
   int bb = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)L, 0.f))) * 0.5f);
   bb = max(0, min(bb, T - 1));
@@ -104,7 +107,7 @@ __device__ __forceinline__ void tile_of(int L, int T, int& a, int& b) {
   a = bb + (L - col_start(bb, T));
 }
 
-__device__ __forceinline__ void tile_next(int& a, int& b, int T) {
+__host__ __device__ __forceinline__ void tile_next(int& a, int& b, int T) {
   if (++a == T) {
     ++b;
     a = b;
@@ -112,7 +115,7 @@ __device__ __forceinline__ void tile_next(int& a, int& b, int T) {
 }
 
 // Move k >= 0 positions forward in the column-major tile list.
-__device__ __forceinline__ void tile_skip(int& a, int& b, int T, int k) {
+__host__ __device__ __forceinline__ void tile_skip(int& a, int& b, int T, int k) {
   a += k;
   while (a >= T && b + 1 < T) {  // column b has rows b .. T-1
     a -= T - (b + 1);
@@ -773,6 +776,70 @@ static cudaError_t launch_class(const CoreDesc* d_desc, int n_items, int smem_by
   prof_end(kCls == 0 ? "core_tridiag.small" : kCls == 1 ? "core_tridiag.medium"
                                                         : "core_tridiag.large", s);
   return cudaGetLastError();
+}
+
+// Host-side checks of the launch planning (no GPU): the tile placement of
+// every class and core size partitions the tile list within the TMEM and
+// shared-memory capacities, the list walk agrees with its closed forms, and
+// the dynamic shared memory of every launch fits a CTA.  Returns an empty
+// string or the first failure.
+std::string tridiag_selftest() {
+  char buf[256];
+  for (int n = 1; n <= 1024; ++n) {
+    const int cls = tridiag_class(n);
+    if ((n <= 192) != (cls == 0) || (n > 192 && n <= 320) != (cls == 1))
+      return "launch class of n = " + std::to_string(n);
+    const int class_max = cls == 0 ? 192 : cls == 1 ? 320 : 1024;
+    for (int n_max = n; n_max <= class_max; ++n_max) {
+      const int smem = tridiag_smem_bytes(cls, n_max);
+      if (smem <= 0 || smem > 227 * 1024) {
+        snprintf(buf, sizeof buf, "shared memory %d B for class %d, n_max %d", smem, cls, n_max);
+        return buf;
+      }
+      const TileLayout L = tile_layout(n, kTmemColsOf[cls], smem, n_max);
+      const int nt = tiles_in(L.T);
+      // shared memory holds kVecs padded vectors, the reduction buffer and
+      // the shared tiles; TMEM holds 128 lanes x its columns f32 cells
+      const int64_t npad = (n_max + kTile - 1) / kTile * kTile;
+      const int64_t smem_need =
+          4 * ((int64_t)kVecs * npad + kRed + (int64_t)(L.Lt - L.Lg) * kTileFloats);
+      const bool ok = L.T == (n + kTile - 1) / kTile && 0 <= L.Lg && L.Lg <= L.Lt &&
+                      L.Lt <= nt && L.Ntm == nt - L.Lt &&
+                      (int64_t)L.Ntm * kTileFloats <= 128LL * kTmemColsOf[cls] &&
+                      smem_need <= smem &&
+                      tridiag_work_floats(cls, n, n_max) == (int64_t)L.Lg * kTileFloats;
+      bool col_boundary = false;
+      for (int g = 0; g <= L.T; ++g) col_boundary |= col_start(g, L.T) == L.Lg;
+      if (!ok || !col_boundary) {
+        snprintf(buf, sizeof buf, "tile layout n = %d, class %d, n_max %d: T %d Lg %d Lt %d Ntm %d",
+                 n, cls, n_max, L.T, L.Lg, L.Lt, L.Ntm);
+        return buf;
+      }
+    }
+  }
+  for (int T = 1; T <= 48; ++T) {
+    const int nt = tiles_in(T);
+    int a = 0, b = 0;
+    for (int L = 0; L < nt; ++L) {
+      int a2, b2;
+      tile_of(L, T, a2, b2);
+      if (a2 != a || b2 != b || a < b || a >= T || col_start(b, T) + (a - b) != L) {
+        snprintf(buf, sizeof buf, "tile list walk T = %d at %d", T, L);
+        return buf;
+      }
+      for (int k = 0; L + k < nt; k += 1 + k / 3) {
+        int a3 = a, b3 = b, a4, b4;
+        tile_skip(a3, b3, T, k);
+        tile_of(L + k, T, a4, b4);
+        if (a3 != a4 || b3 != b4) {
+          snprintf(buf, sizeof buf, "tile skip T = %d from %d by %d", T, L, k);
+          return buf;
+        }
+      }
+      tile_next(a, b, T);
+    }
+  }
+  return "";
 }
 
 cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,

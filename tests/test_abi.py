@@ -88,3 +88,14 @@ def test_binding_checks_row_counts_before_any_call():
         csvd.block(torch.zeros(7, 2), 8)
     with pytest.raises(ValueError, match="rows, expected m = 8"):
         csvd._blocks([torch.zeros(7, 2), torch.zeros(8, 2)], 8)
+
+
+def test_launch_planning_selftest_without_gpu(so):
+    """The library's host-side planning checks (eigen-core tile placement for
+    every launch class and core size, the tile-list walk, launch shared
+    memory, one-column row grouping) pass without a GPU."""
+    so.csvd_selftest.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+    buf = ctypes.create_string_buffer(512)
+    rc = so.csvd_selftest(buf, len(buf))
+    assert rc == 0, buf.value.decode()
+    assert buf.value == b"ok"

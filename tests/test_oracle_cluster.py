@@ -132,3 +132,19 @@ def test_compression_ratio_closed_form():
     assert math.isclose(got, 4 * m * n / (r * (m + 4 * n)))
     got = cluster.compression_ratio([[0], [1]], [3, 3], 10, 5)
     assert got == 1.0
+
+
+def test_frobenius_scan_repeats_until_nothing_joins():
+    """Alg. 3, r = 1, eps = 0.09, blocks 10 e1 (anchor), 1 e2, 5 e1.  The
+    ascending scan first offers 1 e2: one direction is discarded (energy 1 of
+    101, relative error 0.0995 > 0.09) and it is refused; 5 e1 joins with
+    nothing discarded; the next scan offers 1 e2 again, now 1 of 126
+    (0.0891 <= 0.09), and it joins."""
+    e = np.eye(3)
+    blocks = [10.0 * e[:, [0]], 1.0 * e[:, [1]], 5.0 * e[:, [0]]]
+    out = cluster.cluster(blocks, 1, 0.09, "approx", "frobenius")
+    assert out["clusters"] == [[0, 2, 1]]
+    first = out["log"][0]
+    assert first[1] == 1 and not first[4]
+    assert first[2] == pytest.approx(1.0) and first[3] == pytest.approx(101.0)
+    assert out["estimate_sq"][0] == pytest.approx(1.0)

@@ -472,7 +472,9 @@ def main():
     ap.add_argument("--n-states", type=int, default=64)
     ap.add_argument("--per-state", type=int, default=64)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20,
+                    help="end-to-end steps; the first copy cannot overlap a step, so more "
+                         "steps weigh the pipeline fill less")
     ap.add_argument("--ref-sample", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--parity-samples", type=int, default=8)

@@ -394,27 +394,38 @@ static bool arrow_eligible(const Item& it) {
 
 static_assert(sizeof(ArrowDesc) % alignof(int2) == 0, "group table follows the descriptors");
 
-static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, cudaStream_t s,
-                                   int* d_status) {
+static bool same_arrow_state(const Item& x, const Item& y) {
+  return x.st.U == y.st.U && x.st.ldu == y.st.ldu && x.st.rt == y.st.rt && x.r == y.r &&
+         x.m == y.m && x.st.sigma == y.st.sigma && x.st.scal == y.st.scal;
+}
+
+// One-column items in launch order (candidates of one state side by side)
+// and their CTA groups {first position in that order, count <= kArrowGroup},
+// each group one state.
+static void arrow_item_groups(const std::vector<Item>& items, std::vector<int>& order,
+                              std::vector<int2>& groups) {
   const int n = (int)items.size();
-  if (n == 0) return CSVD_OK;
-  // candidates of one state side by side, in groups of up to kArrowGroup
-  std::vector<int> order(n);
+  order.resize(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return reinterpret_cast<uintptr_t>(items[x].st.U) < reinterpret_cast<uintptr_t>(items[y].st.U);
   });
-  auto same_state = [&](const Item& x, const Item& y) {
-    return x.st.U == y.st.U && x.st.ldu == y.st.ldu && x.st.rt == y.st.rt && x.r == y.r &&
-           x.m == y.m && x.st.sigma == y.st.sigma && x.st.scal == y.st.scal;
-  };
-  std::vector<int2> groups;
+  groups.clear();
   for (int i = 0; i < n; ++i) {
     if (groups.empty() || groups.back().y == kArrowGroup ||
-        !same_state(items[order[i]], items[order[groups.back().x]]))
+        !same_arrow_state(items[order[i]], items[order[groups.back().x]]))
       groups.push_back(make_int2(i, 0));
     ++groups.back().y;
   }
+}
+
+static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, cudaStream_t s,
+                                   int* d_status) {
+  const int n = (int)items.size();
+  if (n == 0) return CSVD_OK;
+  std::vector<int> order;
+  std::vector<int2> groups;
+  arrow_item_groups(items, order, groups);
   std::vector<ArrowDesc> ad(n);
   for (int i = 0; i < n; ++i) {
     const Item& it = items[order[i]];
@@ -1229,6 +1240,44 @@ csvd_status csvd_selftest(char* msg, int64_t cap) {
       }
       for (int j = 0; j < n && err.empty(); ++j)
         if (seen[j] != 1) err = "row not covered exactly once";
+    }
+    // CTA groups of one-column items handed to csvd_score: fake states
+    // (pointers compared, never dereferenced), some sharing U but not r
+    for (int trial = 0; trial < 500 && err.empty(); ++trial) {
+      // states 3t, 3t+1, 3t+2 share U and r_t; 3t+1 differs from 3t only in
+      // r, 3t+2 only in sigma and the energy scalars
+      const int n = 1 + next(150), n_states = 1 + next(9);
+      std::vector<Item> items(n);
+      std::vector<int> sid(n);
+      for (int i = 0; i < n; ++i) {
+        const int si = sid[i] = next(n_states), t = si / 3, u = si % 3;
+        Item& it = items[i];
+        it.st.U = reinterpret_cast<const float*>(uintptr_t(0x10000) * (uintptr_t)(1 + t));
+        it.st.ldu = 32;
+        it.st.rt = 8 + t;
+        it.st.r = it.r = 16 + (u == 1 ? 1 : 0);
+        it.st.sigma = reinterpret_cast<const float*>(uintptr_t(0x900000) + 64 * (uintptr_t)(3 * t + (u == 2 ? 2 : 0)));
+        it.st.scal = reinterpret_cast<const double*>(uintptr_t(0xA00000) + 64 * (uintptr_t)(3 * t + (u == 2 ? 2 : 0)));
+        it.m = 64;
+      }
+      std::vector<int> order;
+      std::vector<int2> groups;
+      arrow_item_groups(items, order, groups);
+      std::vector<int> seen(n, 0), pos_seen(n, 0);
+      for (int i : order) ++seen[i];
+      int next_pos = 0;
+      for (const int2& g : groups) {
+        if (g.x != next_pos || g.y < 1 || g.y > kArrowGroup || g.x + g.y > n) {
+          err = "item groups not a partition of the order";
+          break;
+        }
+        for (int t = 0; t < g.y; ++t)
+          if (sid[order[g.x + t]] != sid[order[g.x]]) err = "item group mixes states";
+        next_pos += g.y;
+      }
+      if (err.empty() && next_pos != n) err = "item groups do not cover the order";
+      for (int i = 0; i < n && err.empty(); ++i)
+        if (seen[i] != 1) err = "item order not a permutation";
     }
   }
   if (msg && cap > 0) {

@@ -195,7 +195,8 @@ csvd_status csvd_stream_free(csvd_stream s);
  * needed: the tile placement of the eigen core for every launch class and
  * core size (tiles partitioned among global memory, shared memory and
  * TMEM within their capacities), its tile-list walk, the launch classes'
- * shared memory, and the row grouping of csvd_score_columns.  Writes "ok"
+ * shared memory, the row grouping of csvd_score_columns and the grouping
+ * of one-column candidates of csvd_score into CTAs.  Writes "ok"
  * or the first failure into msg (cap bytes, may be NULL); returns CSVD_OK
  * or CSVD_ERR_SHAPE. */
 csvd_status csvd_selftest(char* msg, int64_t cap);

@@ -56,10 +56,18 @@ typedef enum { CSVD_F32 = 0, CSVD_BF16 = 1 } csvd_dtype;
  *     P = U^T A, R = A - U P with one re-orthogonalisation pass, Householder
  *     QR of R, one-sided Jacobi SVD of the core K.
  *   CSVD_MIXED -- the same quantities from one pass over A on the tensor
- *     cores: P = U^T A and A^T A (bf16 split operands, FP32 accumulation), the
- *     core's eigenvalues from the Gram K^T K = [[S, diag(s) P],[P^T diag(s),
- *     A^T A]] by Householder tridiagonalisation and bisection; tails in FP64. */
-typedef enum { CSVD_PLAIN_FP32 = 0, CSVD_MIXED = 1 } csvd_precision;
+ *     cores: P = U^T A and A^T A (tf32 split operands hi + lo, three MMAs per
+ *     product, FP32 accumulation; the diagonal of A^T A replaced by exact
+ *     column energies), the core's eigenvalues from the Gram K^T K =
+ *     [[S, diag(s) P],[P^T diag(s), A^T A]] by Householder tridiagonalisation
+ *     and bisection; tails in FP64.  Cores whose estimated tail is too small
+ *     for FP32 eigenvalues to resolve it (E~^2 below 2e-3 of the merged
+ *     energy) are solved again in FP64 from the same Gram.
+ *   CSVD_GRAM_FP32 -- the CSVD_MIXED route with the two products taken by
+ *     FP32 SIMT GEMMs instead of the tensor cores (the plain-FP32 form of the
+ *     same algorithm).  Blocks with k = 1 take the arrowhead core in both.
+ * Basis commits (csvd_incr_append) always take the CSVD_PLAIN_FP32 step. */
+typedef enum { CSVD_PLAIN_FP32 = 0, CSVD_MIXED = 1, CSVD_GRAM_FP32 = 2 } csvd_precision;
 
 typedef enum { CSVD_ALG_WEYL = 1, CSVD_ALG_RESIDUAL = 2, CSVD_ALG_APPROX = 3 } csvd_algo;
 typedef enum { CSVD_SORT_FROBENIUS = 0, CSVD_SORT_RESIDUAL = 1 } csvd_sort;

@@ -267,6 +267,10 @@ static csvd_status take_status(int* d_status, cudaStream_t s) {
 
 // Largest core kept in shared memory (bytes of dynamic shared memory).
 static constexpr int kCoreSmemBudget = 200 * 1024;
+// FP64 re-solve of the mixed core: at most this many persistent CTAs, and at
+// most this many bytes of slots per call (at least one slot)
+static constexpr int kRefineSlots = 64;
+static constexpr size_t kRefineBytes = size_t(192) << 20;
 
 static int num_sms();
 namespace csvd {
@@ -298,9 +302,9 @@ static bool gram_on_tensor_cores() {
 }
 
 // ------------------------------------------------------- TMA tensor maps
-// 2-D maps (box: 32 rows x 128 f32 columns, no swizzle, zero fill) of the
-// candidate blocks and state bases read by the tensor-core Gram; encoded on
-// the host through the driver entry point and cached by (address, shape).
+// 2-D maps of the candidate blocks and state bases read by the tensor-core
+// Gram (tc_tensor_map: box 32 rows x 32 f32 columns, 128-byte swizzle, zero
+// fill), cached by (address, shape).
 struct MapKey {
   uintptr_t ptr;
   int64_t cols, rows, ld;
@@ -320,22 +324,8 @@ struct MapKeyHash {
 static std::mutex g_map_mu;
 static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_maps;
 
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
 // Tensor map of a row-major f32 matrix (rows x cols, leading dimension ld);
-// false when it cannot be encoded (the kernel then copies row by row).
+// false when it cannot be encoded (the item then takes the SIMT Gram).
 static bool tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out) {
   const MapKey key{reinterpret_cast<uintptr_t>(ptr), cols, rows, ld};
   std::lock_guard<std::mutex> lk(g_map_mu);
@@ -344,17 +334,8 @@ static bool tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, 
     *out = it->second;
     return true;
   }
-  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)kTcBN, (cuuint32_t)kTcBK};
-  cuuint32_t es[2] = {1, 1};
   CUtensorMap m;
-  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
-         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
+  if (!tc_tensor_map(ptr, cols, rows, ld, &m)) return false;
   if (g_maps.size() > (1u << 20)) g_maps.clear();
   g_maps.emplace(key, m);
   *out = m;
@@ -467,7 +448,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
 static csvd_status run_items(const std::vector<Item>& items, double eps, int precision,
                              cudaStream_t s, int* d_status, Workspace& ws, CommitKeep* keep,
                              bool want_W) {
-  if (precision == CSVD_MIXED && !want_W) {
+  if (precision != CSVD_PLAIN_FP32 && !want_W) {
     std::vector<Item> arrow, rest;
     for (const Item& it : items) (arrow_eligible(it) ? arrow : rest).push_back(it);
     if (!arrow.empty()) {
@@ -485,10 +466,18 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   const int n = (int)items.size();
   if (n == 0) return CSVD_OK;
   Layout L;
-  struct Off { size_t energy, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new, cls; bool smem; };
+  struct Off { size_t energy, colE, P, P2, Rt, tau, B, G, work, Wt; int64_t ldwork; int kp, nr, nc, r_new, cls; bool smem; };
   std::vector<Off> off(n);
-  const bool mixed = (precision == CSVD_MIXED) && !want_W;
+  // the Gram route (tensor-core products for CSVD_MIXED, FP32 SIMT products
+  // for CSVD_GRAM_FP32); the plain route also serves basis commits
+  const bool mixed = (precision != CSVD_PLAIN_FP32) && !want_W;
+  const bool tensor = mixed && precision == CSVD_MIXED && gram_on_tensor_cores();
   const size_t energies = L.add(sizeof(double) * (size_t)n);  // one array, zeroed at once
+  // mixed: the column energies of every block, one array zeroed at once
+  size_t colE_total = 0;
+  if (mixed)
+    for (int i = 0; i < n; ++i) colE_total += (size_t)items[i].blk->k;
+  const size_t colE_base = mixed ? L.add(sizeof(double) * colE_total) : 0;
   for (int i = 0; i < n; ++i) {
     const Item& it = items[i];
     const int64_t m = it.m;
@@ -499,6 +488,12 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
     o.nc = rt + k;
     o.r_new = std::min(it.r, o.nr);
     o.energy = energies + sizeof(double) * (size_t)i;
+    o.colE = 0;
+    if (mixed) {
+      size_t before = 0;
+      for (int j = 0; j < i; ++j) before += (size_t)items[j].blk->k;
+      o.colE = colE_base + sizeof(double) * before;
+    }
     // mixed form: P and A^T A rows padded to 4 floats (16-byte stores)
     const int kld = mixed ? (k + 3) & ~3 : k;
     o.P = rt > 0 ? L.add(sizeof(float) * (size_t)rt * kld) : 0;
@@ -524,6 +519,20 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   // mixed form: eigen-core launch classes by core size; the leading tile
   // columns of the largest cores get a global workspace
   int tri_nmax[3] = {1, 1, 1};
+  // mixed form: per-item FP64 re-solve marks, the persistent re-solve's item
+  // counter and its workspace slots (n_max^2 doubles each)
+  size_t refine_flags = 0, refine_ctr = 0, refine_work = 0;
+  int refine_slots = 0, refine_nmax = 1;
+  if (mixed) {
+    for (int i = 0; i < n; ++i)
+      refine_nmax = std::max(refine_nmax, items[i].st.rt + (int)items[i].blk->k);
+    const size_t slot_bytes = sizeof(double) * (size_t)refine_nmax * refine_nmax;
+    refine_slots = (int)std::min<size_t>({(size_t)n, (size_t)kRefineSlots,
+                                          std::max<size_t>(1, kRefineBytes / slot_bytes)});
+    refine_flags = L.add((size_t)n);
+    refine_ctr = L.add(sizeof(int));
+    refine_work = L.add(slot_bytes * (size_t)refine_slots);
+  }
   if (mixed) {
     for (int i = 0; i < n; ++i) {
       const int nn = items[i].st.rt + (int)items[i].blk->k;
@@ -538,7 +547,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   }
   // tensor-core Gram: eligible items (f32, 16-byte aligned rows)
   std::vector<char> tc_ok(n, 0);
-  if (mixed && gram_on_tensor_cores()) {
+  if (tensor) {
     for (int i = 0; i < n; ++i) {
       const Item& it = items[i];
       const bool a_ok = it.blk->dtype == CSVD_F32 && (reinterpret_cast<uintptr_t>(it.blk->ptr) & 15) == 0 &&
@@ -557,6 +566,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
     for (int i = 0; i < n; ++i) {
       if (!tc_ok[i]) continue;
       const Item& it = items[i];
+      tc_ok[i] = 0;  // set again once both maps exist
       CUtensorMap ma;
       if (!tensor_map(it.blk->ptr, it.blk->k, it.m, it.blk->ld, &ma)) continue;
       int iu = -1;
@@ -565,7 +575,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
           if (pr.first == it.st.U) iu = pr.second;
         if (iu < 0) {
           CUtensorMap mu;
-          if (!tensor_map(it.st.U, it.st.ldu, it.m, it.st.ldu, &mu)) continue;
+          if (!tensor_map(it.st.U, it.st.rt, it.m, it.st.ldu, &mu)) continue;
           iu = (int)maps.size();
           maps.push_back(mu);
           seenU.push_back({it.st.U, iu});
@@ -574,12 +584,13 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
       mapA_idx[i] = (int)maps.size();
       maps.push_back(ma);
       mapU_idx[i] = iu;
+      tc_ok[i] = 1;
     }
   }
   char* pk_base = nullptr;  // device address of the descriptor region (maps first)
   auto build = [&](char* base, Pack& pk, GemmBatch& gP, GemmBatch& gR, GemmBatch& gP2,
                    GemmBatch& gRu, GemmBatch& gG, std::vector<EnergyDesc>& ed,
-                   std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
+                   std::vector<EnergyDesc>& ced, std::vector<QRDesc>& qd, std::vector<CoreDesc>& cd_s,
                    std::vector<CoreDesc>& cd_g, std::vector<CoreDesc>& cd_m, std::vector<TcItem>& tci,
                    std::vector<TcTile>& tct) {
     pk.add(maps);
@@ -596,7 +607,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
       EnergyDesc e{it.blk->ptr, it.blk->ld, (int)m, k, bf, 0, energy};
       ed.push_back(e);
       const int kld = mixed ? (k + 3) & ~3 : k;
-      if (rt > 0 && !tc_ok[i])
+      if (rt > 0 && !mixed)
         gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, kld, 0, rt, k, (int)m,
                     1.f, nullptr, 0, 0, 0.f, 0, bf));
       CoreDesc c;
@@ -606,7 +617,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
       c.ldp = kld;
       c.sigma = it.st.sigma;
       c.scal = it.st.scal;
-      // mixed form: the eigen core takes ||A||^2 from the trace of A^T A
+      // mixed form: the eigen core takes ||A||^2 as the sum of the column energies
       c.energy_add = mixed ? nullptr : energy;
       c.sigma_out = it.sigma_out;
       c.tail_out = it.tail_out;
@@ -623,26 +634,31 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
       c.ldwork = o.ldwork;
       if (mixed) {
         float* G = reinterpret_cast<float*>(base + o.G);
+        double* colE = reinterpret_cast<double*>(base + o.colE);
         if (tc_ok[i]) {
           const int id = (int)tci.size();
           TcItem ti{reinterpret_cast<const float*>(it.blk->ptr), it.blk->ld, it.st.U,
-                    it.st.ldu, (int)m, k, rt, 0, P, kld, G, kld, nullptr, nullptr};
-          if (mapA_idx[i] >= 0 && (rt == 0 || mapU_idx[i] >= 0)) {
-            // maps are the first array of the descriptor region
-            ti.mapA = pk_base + (size_t)mapA_idx[i] * sizeof(CUtensorMap);
-            ti.mapU = rt > 0 ? pk_base + (size_t)mapU_idx[i] * sizeof(CUtensorMap) : ti.mapA;
-          }
+                    it.st.ldu, (int)m, k, rt, 0, P, kld, G, kld, colE, nullptr, nullptr};
+          // maps are the first array of the descriptor region
+          ti.mapA = pk_base + (size_t)mapA_idx[i] * sizeof(CUtensorMap);
+          ti.mapU = rt > 0 ? pk_base + (size_t)mapU_idx[i] * sizeof(CUtensorMap) : ti.mapA;
           tci.push_back(ti);
           for (int r0 = 0; r0 < rt; r0 += kTcBM)
             for (int c0 = 0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 0, r0, c0});
           for (int r0 = 0; r0 < k; r0 += kTcBM)
             for (int c0 = r0; c0 < k; c0 += kTcBN) tct.push_back(TcTile{id, 1, r0, c0});
         } else {
+          if (rt > 0)
+            gP.add(gemm(it.st.U, it.st.ldu, 1, it.blk->ptr, it.blk->ld, 0, P, kld, 0, rt, k, (int)m,
+                        1.f, nullptr, 0, 0, 0.f, 0, bf));
           gG.add(gemm(it.blk->ptr, it.blk->ld, 1, it.blk->ptr, it.blk->ld, 0, G, kld, 0, k, k,
                       (int)m, 1.f, nullptr, 0, 0, 0.f, bf, bf), true);
+          ced.push_back(EnergyDesc{it.blk->ptr, it.blk->ld, (int)m, k, bf, 0, colE});
         }
         c.Gaa = G;
+        c.colE = colE;
         c.ldb = kld;
+        c.refine = reinterpret_cast<uint8_t*>(base + refine_flags) + i;
         c.work = o.work ? reinterpret_cast<float*>(base + o.work) : nullptr;
       } else {
         if (bf) return false;
@@ -680,12 +696,12 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   {
     Pack pk;
     GemmBatch a, b, c, d, e;
-    std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg, cm;
+    std::vector<EnergyDesc> ed, ce; std::vector<QRDesc> qd; std::vector<CoreDesc> cs, cg, cm;
     std::vector<TcItem> ti; std::vector<TcTile> tt;
     char* fake = reinterpret_cast<char*>(uintptr_t(1) << 20);
-    if (!build(fake, pk, a, b, c, d, e, ed, qd, cs, cg, cm, ti, tt))
+    if (!build(fake, pk, a, b, c, d, e, ed, ce, qd, cs, cg, cm, ti, tt))
       return fail(CSVD_ERR_UNIMPLEMENTED, "bf16 blocks need the mixed form");
-    pk.add(ed); pk.add(qd); pk.add(cs); pk.add(cg); pk.add(cm); pk.add(ti); pk.add(tt);
+    pk.add(ed); pk.add(ce); pk.add(qd); pk.add(cs); pk.add(cg); pk.add(cm); pk.add(ti); pk.add(tt);
     desc_bytes = pk.buf.size();
   }
   const size_t off_desc = L.add(desc_bytes);
@@ -695,22 +711,28 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   pk_base = ws.base + off_desc;
   Pack pk;
   GemmBatch gP, gR, gP2, gRu, gG;
-  std::vector<EnergyDesc> ed; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g, cd_m;
+  std::vector<EnergyDesc> ed, ced; std::vector<QRDesc> qd; std::vector<CoreDesc> cd_s, cd_g, cd_m;
   std::vector<TcItem> tci; std::vector<TcTile> tct;
-  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, qd, cd_s, cd_g, cd_m, tci, tct);
+  build(ws.base, pk, gP, gR, gP2, gRu, gG, ed, ced, qd, cd_s, cd_g, cd_m, tci, tct);
   if (mixed) {
     // one CTA per core, dispatched in descriptor order: the largest cores
     // (cost ~ n^3) first, so the end of each launch is not one big core
     auto larger = [](const CoreDesc& a, const CoreDesc& b) { return a.rt + a.k > b.rt + b.k; };
     for (auto* v : {&cd_s, &cd_m, &cd_g}) std::stable_sort(v->begin(), v->end(), larger);
   }
-  const size_t o_ed = pk.add(ed), o_qd = pk.add(qd), o_cs = pk.add(cd_s), o_cg = pk.add(cd_g);
+  const size_t o_ed = pk.add(ed), o_ce = pk.add(ced), o_qd = pk.add(qd), o_cs = pk.add(cd_s),
+               o_cg = pk.add(cd_g);
   const size_t o_cm = pk.add(cd_m);
   const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);
   char* dbase = ws.base + off_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
-  // block energies start at zero (the mixed form takes them from tr(A^T A))
+  // block energies start at zero (the mixed form sums its column energies)
   if (!mixed) CUDA_TRY(cudaMemsetAsync(ws.base + energies, 0, sizeof(double) * (size_t)n, s));
+  if (mixed) {
+    CUDA_TRY(cudaMemsetAsync(ws.base + colE_base, 0, sizeof(double) * colE_total, s));
+    CUDA_TRY(cudaMemsetAsync(ws.base + refine_flags, 0, (size_t)n, s));
+    CUDA_TRY(cudaMemsetAsync(ws.base + refine_ctr, 0, sizeof(int), s));
+  }
   int max_chunks = 1;
   int max_m = 1;
   for (int i = 0; i < n; ++i) {
@@ -721,6 +743,10 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   if (!mixed) CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
   CUDA_TRY(gP.launch(dbase, s));
   if (mixed) {
+    int max_k = 1;
+    for (const EnergyDesc& e : ced) max_k = std::max(max_k, e.k);
+    CUDA_TRY(launch_col_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ce), (int)ced.size(), max_k,
+                               max_m, s));
     CUDA_TRY(launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti), reinterpret_cast<TcTile*>(dbase + o_tt),
                             (int)tct.size(), num_sms(), d_status, s));
     CUDA_TRY(gG.launch(dbase, s));
@@ -730,6 +756,12 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
                                  tri_nmax[1], d_status, s));
     CUDA_TRY(launch_core_tridiag(0, reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
                                  tri_nmax[0], d_status, s));
+    CUDA_TRY(launch_core_refine64(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
+                                  reinterpret_cast<CoreDesc*>(dbase + o_cm), (int)cd_m.size(),
+                                  reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
+                                  reinterpret_cast<double*>(ws.base + refine_work), refine_slots,
+                                  refine_nmax, reinterpret_cast<int*>(ws.base + refine_ctr),
+                                  d_status, s));
   } else {
     CUDA_TRY(gR.launch(dbase, s));
     CUDA_TRY(gP2.launch(dbase, s));
@@ -866,7 +898,7 @@ csvd_status csvd_incr_init(csvd_state* out, int64_t m, int32_t r, int32_t precis
   *out = nullptr;
   if (m < 1 || m > 65536 || r < 1 || r > 1024 || r > m)
     return fail(CSVD_ERR_ARG, "need 1 <= r <= min(m, 1024), m <= 65536");
-  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED && precision != CSVD_GRAM_FP32)
     return fail(CSVD_ERR_ARG, "bad precision");
   csvd_state_s* st = new csvd_state_s();
   st->m = m;
@@ -974,7 +1006,7 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
                        double* tail_paper_out, uint8_t* accept_out) {
   if (!states || n_states < 1 || !cands || n < 0 || !sigma_out || !tail_sq_out)
     return fail(CSVD_ERR_ARG, "NULL argument");
-  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED && precision != CSVD_GRAM_FP32)
     return fail(CSVD_ERR_ARG, "bad precision");
   if (n == 0) return CSVD_OK;
   const int64_t m = states[0]->m;
@@ -1106,7 +1138,7 @@ csvd_status csvd_stream_init(csvd_stream* out, int64_t m, int32_t r, double eps,
   if (m < 1 || m > 65536 || r < 1 || r > 1024 || r > m)
     return fail(CSVD_ERR_ARG, "need 1 <= r <= min(m, 1024), m <= 65536");
   if (!(eps >= 0.0)) return fail(CSVD_ERR_ARG, "need eps >= 0");
-  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED && precision != CSVD_GRAM_FP32)
     return fail(CSVD_ERR_ARG, "bad precision");
   csvd_stream_s* h = new csvd_stream_s();
   h->m = m;
@@ -1969,7 +2001,7 @@ extern "C" csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t
     return fail(CSVD_ERR_ARG, "bad algo");
   if (sort_mode != CSVD_SORT_FROBENIUS && sort_mode != CSVD_SORT_RESIDUAL)
     return fail(CSVD_ERR_ARG, "bad sort mode");
-  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED)
+  if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED && precision != CSVD_GRAM_FP32)
     return fail(CSVD_ERR_ARG, "bad precision");
   for (int i = 0; i < n; ++i) {
     CSVD_TRY(check_block(&blocks[i], m));

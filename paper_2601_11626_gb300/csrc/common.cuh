@@ -77,6 +77,7 @@ struct CoreDesc {
   const float* B;        // plain: kp x k upper-triangular R factor (ldb)
   const float* Gaa;      // mixed: k x k Gram A^T A (upper triangle valid, ldb)
   int64_t ldb;
+  const double* colE;    // mixed: k column energies sum_i A_ic^2 (the diagonal of A^T A)
   const float* sigma;    // r_t retained singular values of the state
   const double* scal;    // state scalars {energy, discarded}
   const double* energy_add;  // ||A||_F^2 of this block
@@ -89,6 +90,7 @@ struct CoreDesc {
   double* tail_paper_out;// sum ||A||^2 - sum sigma~^2 (may be null)
   double* energy_out;    // ||M||^2 after the append (may be null)
   uint8_t* accept_out;   // may be null
+  uint8_t* refine;       // mixed: set to 1 when the tail needs the FP64 re-solve (may be null)
   double eps;
   int rt, k, kp, r_new;  // r_new = min(r, rt + kp)
   int in_smem, pad;
@@ -188,6 +190,10 @@ cudaError_t launch_apply_q(const ApplyQDesc* d_desc, int n_items, int max_cols,
                            cudaStream_t s);
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
+// Column energies: out[c] += sum_i A_ic^2 for every column of every item
+// (EnergyDesc.out points at k doubles, zeroed before the launch).
+cudaError_t launch_col_energy(const EnergyDesc* d_desc, int n_items, int max_k, int max_m,
+                              cudaStream_t s);
 int jacobi_scratch_floats(int nc);
 // Eigen core launch classes by core size n (0: n <= 192, 1: n <= 320,
 // 2: larger), the dynamic shared memory of a class launch whose largest
@@ -202,6 +208,15 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
 cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
                                 int* d_status, cudaStream_t s);
 std::string tridiag_selftest();
+// The mixed core marks an item for the FP64 re-solve when its estimated tail
+// lies below this fraction of the merged energy.
+constexpr double kRefineFrac = 2e-3;
+// FP64 re-solve of the marked items of up to three core arrays: `slots`
+// persistent CTAs, each with n_max^2 doubles of `work`; *d_counter must be 0.
+size_t refine64_smem_bytes(int n_max);
+cudaError_t launch_core_refine64(const CoreDesc* d0, int n0, const CoreDesc* d1, int n1,
+                                 const CoreDesc* d2, int n2, double* work, int slots, int n_max,
+                                 int* d_counter, int* d_status, cudaStream_t s);
 cudaError_t launch_core_arrow(const ArrowDesc* d_desc, const int2* d_groups, int n_groups,
                               int* d_status, cudaStream_t s);
 // Candidates as rows of one matrix: group g = {first row, count, state, 0};

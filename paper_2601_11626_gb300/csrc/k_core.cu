@@ -56,6 +56,44 @@ cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
   return cudaGetLastError();
 }
 
+// Column energies for blocks the tensor-core Gram does not read: a CTA
+// takes 32 columns and a slice of the rows (one coalesced 128-byte row
+// segment per warp step); squares are summed exactly (FMA for the rounding
+// error of the square, two-sum for the addition) and each warp adds its
+// FP64 totals into the column's slot.
+constexpr int kColRows = 256;  // rows per CTA
+__global__ void __launch_bounds__(256)
+col_energy_kernel(const EnergyDesc* __restrict__ descs) {
+  const EnergyDesc d = descs[blockIdx.z];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int r0 = blockIdx.y * kColRows;
+  if (blockIdx.x * 32 >= d.k || r0 >= d.m) return;
+  float s = 0.f, comp = 0.f;
+  const int r1 = min(d.m, r0 + kColRows);
+  if (c < d.k) {
+    for (int i = r0 + (threadIdx.x >> 5); i < r1; i += 8) {
+      const float x = load_elem(d.A, (int64_t)i * d.ld + c, d.bf16);
+      const float p = x * x;
+      const float e = fmaf(x, x, -p);
+      const float t = s + p;
+      const float z = t - s;
+      comp += ((s - (t - z)) + (p - z)) + e;
+      s = t;
+    }
+    atomicAdd(d.out + c, (double)s + (double)comp);
+  }
+}
+
+cudaError_t launch_col_energy(const EnergyDesc* d_desc, int n_items, int max_k, int max_m,
+                              cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((max_k + 31) / 32, (max_m + kColRows - 1) / kColRows, n_items);
+  prof_begin(s);
+  col_energy_kernel<<<grid, 256, 0, s>>>(d_desc);
+  prof_end("col_energy", s);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ shared epilogue
 // vals[0..nv) non-increasing; writes sigma~, tails and the accept flag.
 // Called by warp 0 only; vals_are_sq says whether vals hold sigma^2.

@@ -1,55 +1,72 @@
 // P = U^T A and G = A^T A for a batch of uneven candidates on the 5th-gen
-// tensor cores (tcgen05), in one pass over each candidate.
+// tensor cores (tcgen05), in one pass over each candidate, together with the
+// exact column energies sum_i A_ic^2.
 //
-// These are the two products the mixed merge evaluation needs: the Gram of
-// the core, K^T K = [[S, diag(s) P], [P^T diag(s), A^T A]], is assembled from
+// These are the products the mixed merge evaluation needs: the Gram of the
+// core, K^T K = [[S, diag(s) P], [P^T diag(s), A^T A]], is assembled from
 // them (Lemma 1 with the residual folded into A^T A = P^T P + B^T B).
 //
-// Accuracy: every f32 operand x is split into bf16 parts x = hi + lo (+ a
-// remainder below 2^-17 |x|); each 16-deep step issues three MMAs,
-// hi*hi + hi*lo + lo*hi, accumulating in f32 in tensor memory, which keeps
-// the products at f32-level accuracy (split-operand emulation, after Ootomo &
-// Yokota 2022).
+// Accuracy: every f32 operand x is split on the CUDA cores into three bf16
+// parts, x = hi + mid + lo exactly (8 significant bits each, no underflow
+// for the magnitudes met here); each 16-deep step issues six kind::f16 MMAs,
+// hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid, accumulating in f32 in
+// tensor memory.  The dropped mid*lo, lo*mid and lo*lo terms are below
+// 2^-25 |x||y| per product (split-operand emulation after Ootomo & Yokota
+// 2022, with three parts), so the products carry FP32-level accuracy and
+// only the FP32 accumulation rounds.  The diagonal of A^T A is replaced by
+// the exact column energies (compensated f32 sums, added in FP64).
+//
+// Layout: TMA lands each stage's 32 rows of both operands in a staging slot
+// as boxes of 32 rows x 32 f32 columns with the 128-byte swizzle.  The split
+// warps re-chunk them, without transposing, into the MN-major
+// 128-byte-swizzled UMMA layout of bf16: per part and operand two atoms of
+// 64 columns x 32 rows (4 KB each, rows 128 bytes apart, 16-byte chunks
+// XOR-ed with the row), 8-row groups 1 KB apart along K.
 //
 // Structure: persistent CTAs walk a list of 128 x 128 output tiles (tiles of
 // one candidate are adjacent so its columns stay in L2 while they are
 // reused).  Warp roles, connected by mbarrier rings:
-//   warp 0      TMA: one 2-D tensor box (32 rows x 128 f32 columns, zero
-//               outside the matrix) per operand into a 5-deep staging ring
-//               (one cp.async.bulk per row when no tensor map is given)
-//   warps 2-17  split staging f32 -> bf16 hi/lo into a 2-deep operand
-//               ring, K-major with the 64-byte swizzle the UMMA
-//               descriptors expect (one 8-deep chunk of one row per thread)
+//   warp 0      TMA: up to four boxes per operand per stage into a 3-deep
+//               staging ring
+//   warps 2-9   split staging f32 into the bf16 parts of a 2-deep operand
+//               ring; on diagonal tiles also the column sums of squares
 //   warp 1      one thread issues tcgen05.mma (M = 128, K = 16, N = the
-//               tile's valid columns rounded up to 16) into a
-//               double-buffered f32 accumulator in TMEM and commits
-//   warps 18-21 tcgen05.ld the finished accumulator and store it
+//               tile's valid columns rounded up to 16) into a fresh f32
+//               accumulator per stage (two in TMEM, alternating) and commits
+//   warps 10-13 add each stage's accumulator into the tile's running sum
+//               (round to nearest, kept in TMEM) and store the last one;
+//               the tensor cores' own accumulation truncates, so a long
+//               chain of additions inside one accumulator would shrink every
+//               sum by about half an ulp per addition
 // Every mbarrier wait is bounded (2 s of device time); on expiry the CTA
 // sets an abort flag, drains its own copies and MMAs, frees TMEM and
 // reports kStatusWaitCap.
+#include <mutex>
+
+#include <cudaTypedefs.h>
+
 #include "tc_gram.cuh"
 
 namespace csvd {
 namespace {
 
-// staging slot: f32 [32][128] for each operand
+// staging slot: A boxes then B boxes (f32); operand slot: parts of A, then of B
 constexpr int kStA = 0;
-constexpr int kStB = kStA + kTcBK * kTcBM * 4;
-static_assert(kStB + kTcBK * kTcBN * 4 == kTcStageF, "staging layout");
-// operand slot: bf16 [128][32] swizzled, hi and lo of each operand
-constexpr int kAhi = 0;
-constexpr int kAlo = kAhi + kTcBM * kTcBK * 2;
-constexpr int kBhi = kAlo + kTcBM * kTcBK * 2;
-constexpr int kBlo = kBhi + kTcBN * kTcBK * 2;
-static_assert(kBlo + kTcBN * kTcBK * 2 == kTcStageB, "operand layout");
+constexpr int kStB = (kTcBM / kTcBox) * kTcBoxBytes;
+constexpr int kOpA = 0;                 // hi, mid, lo of A at kOpA + p * kTcPartBytes
+constexpr int kOpB = 3 * kTcPartBytes;  // hi, mid, lo of B
 constexpr int kOpBase = kTcStagesF * kTcStageF;  // operand ring after the staging ring
+constexpr int kAtomBytes = kTcBK * 128;          // one 64-column bf16 atom of 32 rows
 constexpr uint64_t kWaitNs = 2000000000ull;
+// TMEM columns: two stage accumulators X and the running sum S of a tile
+constexpr uint32_t kXCol0 = 0, kSCol0 = 2 * kTcBN, kTmemCols = 512;
+static_assert(kTcConvWarps == 8, "four split warps per 64-column atom");
 
 // kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, both
-// K-major, N = 128, M = 128.
+// MN-major, M = 128, N = n.
 __device__ __forceinline__ uint32_t idesc_n(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(kTcBM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcBM >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -110,17 +127,8 @@ __device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, volatile 
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-
-// One 2-D tensor box (32 rows x 128 f32 columns starting at column x, row y)
-// into shared memory; out-of-range rows and columns arrive as zeros.
+// One 2-D tensor box (32 rows x 32 f32 columns from column x, row y) into
+// shared memory, 128-byte swizzled; out-of-range elements arrive as zeros.
 __device__ __forceinline__ void tma_box(uint32_t dst, const void* map, int x, int y, uint32_t mbar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -139,14 +147,17 @@ __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
-// 512 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of an MN-major bf16 operand with the
+// 128-byte swizzle: atoms of 64 elements (MN) x 8 rows (K), 1 KB, aligned to
+// 1 KB.  Leading byte offset = the stride between 64-column atoms (4 KB),
+// stride byte offset = the stride between 8-row groups along K (1 KB).
+// Descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)(kAtomBytes >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)4 << 61;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -182,75 +193,94 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Byte offset of the 16-byte chunk (row, chunk) in a K-major 64B-swizzled
-// tile of 32 bf16 per row.
-__device__ __forceinline__ uint32_t sw64_off(int row, int chunk) {
-  const int r8 = row & 7;
-  return (uint32_t)((row >> 3) * 512 + r8 * 64 + ((chunk ^ (r8 >> 1)) & 3) * 16);
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-  return lo | (hi << 16);
-}
-
-// Split 8 f32 values of one row/chunk into hi and lo bf16 chunks
-// (x = hi + lo + a remainder below 2^-17 |x|), two values per conversion.
-__device__ __forceinline__ void split_store(uint8_t* hi_base, uint8_t* lo_base, uint32_t off,
-                                            const float* x) {
-  uint32_t h[4], l[4];
+// Split 8 f32 values into three bf16 parts (x = hi + mid + lo) and store
+// each part as one 16-byte chunk.
+__device__ __forceinline__ void split3_store(uint8_t* hi, uint8_t* mid, uint8_t* lo, uint32_t off,
+                                             const float* x) {
+  uint32_t h[4], md[4], l[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * p], x[2 * p + 1]);
     const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * p] - hf.x, x[2 * p + 1] - hf.y);
+    const float r0 = x[2 * p] - hf.x, r1 = x[2 * p + 1] - hf.y;
+    const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
+    const float2 mf = __bfloat1622float2(mb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
     h[p] = *reinterpret_cast<const uint32_t*>(&hb);
+    md[p] = *reinterpret_cast<const uint32_t*>(&mb);
     l[p] = *reinterpret_cast<const uint32_t*>(&lb);
   }
-  *reinterpret_cast<uint4*>(hi_base + off) = make_uint4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint4*>(lo_base + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(mid + off) = make_uint4(md[0], md[1], md[2], md[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// s + c += x^2 without rounding loss: the square's rounding error by FMA,
+// the sum's by a two-sum.
+__device__ __forceinline__ void acc_sq(float& s, float& c, float x) {
+  const float p = x * x;
+  const float e = fmaf(x, x, -p);
+  const float t = s + p;
+  const float z = t - s;
+  c += ((s - (t - z)) + (p - z)) + e;
+  s = t;
 }
 
 struct TileInfo {
-  const void* mapa;  // tensor maps (null: per-row bulk copies)
+  const void* mapa;
   const void* mapb;
   int xa, xb;        // first column of each operand inside its map
-  const float* Xa;  // rows operand source (U or A), shifted to its first column
-  int64_t lda;
-  const float* Xb;  // columns operand source (A), shifted to its first column
-  int64_t ldb;
   int validA, validB, m;
+  int nbA, nbB;      // boxes loaded per operand
   bool diag;
   float* out;
   int64_t ldo;
+  double* colE;      // column energies of the diagonal tile's columns (or null)
+  int kcols;         // columns of A past col0 (bounds the energy writes)
 };
 
 __device__ __forceinline__ TileInfo tile_info(const TcItem* items, const TcTile& t) {
   const TcItem d = items[t.item];
   TileInfo ti;
   if (t.kind == 0) {
-    ti.Xa = d.U + t.row0;
-    ti.lda = d.ldu;
     ti.validA = min(kTcBM, d.rt - t.row0);
     ti.out = d.P + (int64_t)t.row0 * d.ldp + t.col0;
     ti.ldo = d.ldp;
+    ti.mapa = d.mapU;
   } else {
-    ti.Xa = d.A + t.row0;
-    ti.lda = d.lda;
     ti.validA = min(kTcBM, d.k - t.row0);
     ti.out = d.G + (int64_t)t.row0 * d.ldg + t.col0;
     ti.ldo = d.ldg;
+    ti.mapa = d.mapA;
   }
-  ti.Xb = d.A + t.col0;
-  ti.ldb = d.lda;
-  ti.mapa = (t.kind == 0) ? d.mapU : d.mapA;
   ti.mapb = d.mapA;
   ti.xa = t.row0;
   ti.xb = t.col0;
   ti.validB = min(kTcBN, d.k - t.col0);
   ti.m = d.m;
   ti.diag = (t.kind == 1 && t.row0 == t.col0);
+  ti.nbA = (ti.validA + kTcBox - 1) / kTcBox;
+  ti.nbB = ti.diag ? 0 : (ti.validB + kTcBox - 1) / kTcBox;
+  ti.colE = (ti.diag && d.colE) ? d.colE + t.col0 : nullptr;
+  ti.kcols = d.k - t.col0;
   return ti;
 }
 
@@ -263,32 +293,31 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOpBase + kTcStagesB * kTcStageB);
-  // barrier slots
-  const uint32_t b0 = smem_u32(bars);
   constexpr int F = kTcStagesF, B = kTcStagesB;
+  const uint32_t b0 = smem_u32(bars);
   auto full_st = [&](int s) { return b0 + 8u * s; };
   auto empty_st = [&](int s) { return b0 + 8u * (F + s); };
-  auto full_bf = [&](int s) { return b0 + 8u * (2 * F + s); };
-  auto empty_bf = [&](int s) { return b0 + 8u * (2 * F + B + s); };
-  auto tmem_full = [&](int a) { return b0 + 8u * (2 * F + 2 * B + a); };
-  auto tmem_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + 2 + a); };
+  auto full_op = [&](int s) { return b0 + 8u * (2 * F + s); };
+  auto empty_op = [&](int s) { return b0 + 8u * (2 * F + B + s); };
+  auto x_full = [&](int a) { return b0 + 8u * (2 * F + 2 * B + a); };
+  auto x_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + 2 + a); };
   const uint32_t final_bar = b0 + 8u * (2 * F + 2 * B + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F + 2 * B + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStagesF; ++s) {
+    for (int s = 0; s < F; ++s) {
       mbar_init(full_st(s), 1);
       mbar_init(empty_st(s), kTcConvWarps);
     }
-    for (int s = 0; s < kTcStagesB; ++s) {
-      mbar_init(full_bf(s), kTcConvWarps);
-      mbar_init(empty_bf(s), 1);
+    for (int s = 0; s < B; ++s) {
+      mbar_init(full_op(s), kTcConvWarps);
+      mbar_init(empty_op(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(tmem_full(a), 1);
-      mbar_init(tmem_empty(a), 4);
+      mbar_init(x_full(a), 1);
+      mbar_init(x_empty(a), 4);
     }
     mbar_init(final_bar, 1);
     *abort_flag = 0;
@@ -297,7 +326,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(256)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -311,83 +340,79 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     bool ok = true;
     for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
       const TileInfo ti = tile_info(items, tiles[tt]);
-      const uint32_t bytesA = 4u * (uint32_t)((ti.validA + 3) & ~3);
-      const uint32_t bytesB = ti.diag ? 0u : 4u * (uint32_t)((ti.validB + 3) & ~3);
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
-      const bool use_map = ti.mapa != nullptr && ti.mapb != nullptr;
+      const uint32_t bytes = (uint32_t)(ti.nbA + ti.nbB) * (uint32_t)kTcBoxBytes;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int slot = it % kTcStagesF;
-        const uint32_t ph = (it / kTcStagesF) & 1u;
+        const int slot = it % F;
+        const uint32_t ph = (it / F) & 1u;
         if (!warp_wait(empty_st(slot), ph ^ 1u, abort_flag)) { ok = false; break; }
-        if (use_map) {
-          // one tensor box per operand: full box bytes (zero-filled outside)
-          if (lane == 0) {
-            uint8_t* st = smem + slot * kTcStageF;
-            const uint32_t box = (uint32_t)(kTcBK * kTcBM * 4);
-            mbar_arrive_tx(full_st(slot), ti.diag ? box : 2u * box);
-            tma_box(smem_u32(st + kStA), ti.mapa, ti.xa, kb * kTcBK, full_st(slot));
-            if (!ti.diag) tma_box(smem_u32(st + kStB), ti.mapb, ti.xb, kb * kTcBK, full_st(slot));
-          }
-          __syncwarp();
-          continue;
-        }
-        const int rows = min(kTcBK, ti.m - kb * kTcBK);
-        if (lane == 0) mbar_arrive_tx(full_st(slot), (uint32_t)rows * (bytesA + bytesB));
-        __syncwarp();
-        if (lane < rows) {
-          const int64_t l = (int64_t)kb * kTcBK + lane;
+        if (lane == 0) {
           uint8_t* st = smem + slot * kTcStageF;
-          bulk_g2s(smem_u32(st + kStA + lane * (kTcBM * 4)), ti.Xa + l * ti.lda, bytesA,
-                   full_st(slot));
-          if (!ti.diag)
-            bulk_g2s(smem_u32(st + kStB + lane * (kTcBN * 4)), ti.Xb + l * ti.ldb, bytesB,
-                     full_st(slot));
+          mbar_arrive_tx(full_st(slot), bytes);
+          for (int j = 0; j < ti.nbA; ++j)
+            tma_box(smem_u32(st + kStA + j * kTcBoxBytes), ti.mapa, ti.xa + j * kTcBox,
+                    kb * kTcBK, full_st(slot));
+          for (int j = 0; j < ti.nbB; ++j)
+            tma_box(smem_u32(st + kStB + j * kTcBoxBytes), ti.mapb, ti.xb + j * kTcBox,
+                    kb * kTcBK, full_st(slot));
         }
+        __syncwarp();
       }
     }
     // drain copies still in flight (all consumed on a normal exit)
     if (lane == 0) {
-      const uint32_t n_last = it < (uint32_t)kTcStagesF ? it : (uint32_t)kTcStagesF;
+      const uint32_t n_last = it < (uint32_t)F ? it : (uint32_t)F;
       for (uint32_t j = it - n_last; j < it; ++j)
-        mbar_wait(full_st(j % kTcStagesF), (j / kTcStagesF) & 1u, abort_flag, false);
+        mbar_wait(full_st(j % F), (j / F) & 1u, abort_flag, false);
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA
+    // Every stage (32 rows) goes into a fresh accumulator X[it % 2]; the
+    // epilogue adds the stages with round-to-nearest (the accumulator itself
+    // truncates each addition).  Within a stage the ten small cross terms
+    // come first and the two hi*hi products last, so the truncated additions
+    // act on small partial sums.
     if (lane == 0) {
-      uint32_t it = 0, tc = 0;
+      uint32_t it = 0;
       bool ok = true;
-      for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x, ++tc) {
+      for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
         const TileInfo ti = tile_info(items, tiles[tt]);
         const int nkb = (ti.m + kTcBK - 1) / kTcBK;
-        const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
-        if (!mbar_wait(tmem_empty(acc), aph ^ 1u, abort_flag)) break;
-        tc_fence_after();
-        const uint32_t dt = tmem_base + acc * (uint32_t)kTcBN;
         // N = the valid columns rounded up to 16: columns past them are not stored
         const uint32_t idesc = idesc_n(min(kTcBN, (ti.validB + 15) & ~15));
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int slot = it % kTcStagesB;
-          const uint32_t ph = (it / kTcStagesB) & 1u;
-          if (!mbar_wait(full_bf(slot), ph, abort_flag)) { ok = false; break; }
+          const int slot = it % B;
+          const uint32_t xb = it & 1u;
+          if (!mbar_wait(x_empty(xb), ((it >> 1) & 1u) ^ 1u, abort_flag) ||
+              !mbar_wait(full_op(slot), (it / B) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          uint8_t* st = smem + kOpBase + slot * kTcStageB;
-          const uint32_t ahi = smem_u32(st + kAhi), alo = smem_u32(st + kAlo);
-          const uint32_t bhi = ti.diag ? ahi : smem_u32(st + kBhi);
-          const uint32_t blo = ti.diag ? alo : smem_u32(st + kBlo);
+          const uint32_t dt = tmem_base + kXCol0 + xb * (uint32_t)kTcBN;
+          const uint32_t op = smem_u32(smem + kOpBase + slot * kTcStageB);
+          const uint32_t a0 = op + kOpA, b0p = ti.diag ? a0 : op + kOpB;
+          uint32_t accf = 0u;
 #pragma unroll
-          for (int s = 0; s < kTcBK / 16; ++s) {
-            const uint32_t o = s * 32;  // 16 bf16 along K
-            const uint64_t dah = sw64_desc(ahi + o), dal = sw64_desc(alo + o);
-            const uint64_t dbh = sw64_desc(bhi + o), dbl = sw64_desc(blo + o);
-            umma(dt, dah, dbh, idesc, (kb | s) != 0 ? 1u : 0u);
-            umma(dt, dah, dbl, idesc, 1u);
-            umma(dt, dal, dbh, idesc, 1u);
+          for (int s16 = 0; s16 < kTcBK / 16; ++s16) {
+            const uint32_t o = s16 * 2048;  // rows 16 s16 .. 16 s16 + 15 of each atom
+            const uint64_t ah = mn_sw128_desc(a0 + o), am = mn_sw128_desc(a0 + kTcPartBytes + o),
+                           al = mn_sw128_desc(a0 + 2 * kTcPartBytes + o);
+            const uint64_t bh = mn_sw128_desc(b0p + o), bm = mn_sw128_desc(b0p + kTcPartBytes + o),
+                           bl = mn_sw128_desc(b0p + 2 * kTcPartBytes + o);
+            umma(dt, am, bm, idesc, accf);
+            accf = 1u;
+            umma(dt, al, bh, idesc, 1u);
+            umma(dt, ah, bl, idesc, 1u);
+            umma(dt, am, bh, idesc, 1u);
+            umma(dt, ah, bm, idesc, 1u);
           }
-          umma_commit(empty_bf(slot));
+#pragma unroll
+          for (int s16 = 0; s16 < kTcBK / 16; ++s16) {
+            const uint32_t o = s16 * 2048;
+            umma(dt, mn_sw128_desc(a0 + o), mn_sw128_desc(b0p + o), idesc, 1u);
+          }
+          umma_commit(empty_op(slot));
+          umma_commit(x_full(xb));
         }
-        if (!ok) break;
-        umma_commit(tmem_full(acc));
       }
       // all issued MMAs complete before TMEM is released
       umma_commit(final_bar);
@@ -396,114 +421,184 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     __syncwarp();
   } else if (warp < 2 + kTcConvWarps) {
     // ---------------------------------------------------- converters
-    // Thread -> (row, 8-deep chunk).  Rows past an operand's valid extent
-    // are not split: they only feed output rows / columns that are never
-    // stored (each output element depends on one row of each operand).
-    const int tc = threadIdx.x - 64;  // 0 .. 32 kTcConvWarps - 1
-    const int row = tc & 127;
-    const int c = tc >> 7;
+    // Warp w splits rows 8 (w % 4) .. + 7 of the 64-column atom w / 4 of each
+    // operand.  Lane l writes bf16 chunk l % 8 (columns 64 (w / 4) + 8 (l % 8)
+    // .. + 7) of rows 8 (w % 4) + 4 i + l / 8: a quarter warp writes one
+    // whole 128-byte row (bank-conflict free) and reads the two f32 chunks
+    // holding its eight columns, odd chunk first in the upper half of the
+    // quarter so that its reads hit distinct banks.  Each thread keeps the
+    // same eight columns, for the column energies.
+    const int w = warp - 2;
+    const int jb = w >> 2;                // bf16 atom (64 columns)
+    const int cb = lane & 7;              // bf16 chunk in the row
+    const int jf = 2 * jb + (cb >> 2);    // f32 box holding its columns
+    const int lc0 = 2 * (cb & 3);         // first f32 chunk in that box
+    const int swap = cb >> 2;
+    const int rbase = 8 * (w & 3) + (lane >> 3);
     uint32_t it = 0;
     bool ok = true;
     for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
       const TileInfo ti = tile_info(items, tiles[tt]);
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
-      const bool masked = ti.mapa == nullptr || ti.mapb == nullptr;
+      const bool do_a = 64 * jb < ti.validA, do_b = !ti.diag && 64 * jb < ti.validB;
+      const bool energies = ti.colE != nullptr && do_a;
+      float es[8], ec[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) es[e] = ec[e] = 0.f;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int fs = it % kTcStagesF, bs = it % kTcStagesB;
-        if (!warp_wait(full_st(fs), (it / kTcStagesF) & 1u, abort_flag)) { ok = false; break; }
-        if (!warp_wait(empty_bf(bs), ((it / kTcStagesB) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        const int fs = it % F, bs = it % B;
+        if (!warp_wait(full_st(fs), (it / F) & 1u, abort_flag)) { ok = false; break; }
+        if (!warp_wait(empty_op(bs), ((it / B) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         const uint8_t* st = smem + fs * kTcStageF;
         uint8_t* op = smem + kOpBase + bs * kTcStageB;
-        const float* sa = reinterpret_cast<const float*>(st + kStA);
-        const float* sb = reinterpret_cast<const float*>(st + kStB);
-        const uint32_t off = sw64_off(row, c);
-        const bool do_a = row < ti.validA, do_b = !ti.diag && row < ti.validB;
-        float x[8];
-        if (masked) {
-          // per-row copies leave rows past m unwritten: zero the K tail
-          const int lmax = ti.m - kb * kTcBK;
-          if (do_a) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = (c * 8 + e < lmax) ? sa[(c * 8 + e) * kTcBM + row] : 0.f;
-            split_store(op + kAhi, op + kAlo, off, x);
+        for (int i = 0; i < 2; ++i) {
+          const int r = rbase + 4 * i;
+          const uint32_t src = (uint32_t)(jf * kTcBoxBytes + r * 128);
+          const uint32_t c0 = (uint32_t)(((lc0 + swap) ^ (r & 7)) << 4);
+          const uint32_t c1 = (uint32_t)(((lc0 + 1 - swap) ^ (r & 7)) << 4);
+          const uint32_t dst = (uint32_t)(jb * kAtomBytes + r * 128 + ((cb ^ (r & 7)) << 4));
+          float x[8];
+          if (do_a) {
+            const float4 u = *reinterpret_cast<const float4*>(st + kStA + src + c0);
+            const float4 v = *reinterpret_cast<const float4*>(st + kStA + src + c1);
+            const float4 p0 = swap ? v : u, p1 = swap ? u : v;
+            x[0] = p0.x; x[1] = p0.y; x[2] = p0.z; x[3] = p0.w;
+            x[4] = p1.x; x[5] = p1.y; x[6] = p1.z; x[7] = p1.w;
+            split3_store(op + kOpA, op + kOpA + kTcPartBytes, op + kOpA + 2 * kTcPartBytes, dst, x);
+            if (energies) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) acc_sq(es[e], ec[e], x[e]);
+            }
           }
           if (do_b) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = (c * 8 + e < lmax) ? sb[(c * 8 + e) * kTcBN + row] : 0.f;
-            split_store(op + kBhi, op + kBlo, off, x);
-          }
-        } else {
-          // tensor boxes arrive zero-filled outside the matrix
-          if (do_a) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = sa[(c * 8 + e) * kTcBM + row];
-            split_store(op + kAhi, op + kAlo, off, x);
-          }
-          if (do_b) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = sb[(c * 8 + e) * kTcBN + row];
-            split_store(op + kBhi, op + kBlo, off, x);
+            const float4 u = *reinterpret_cast<const float4*>(st + kStB + src + c0);
+            const float4 v = *reinterpret_cast<const float4*>(st + kStB + src + c1);
+            const float4 p0 = swap ? v : u, p1 = swap ? u : v;
+            x[0] = p0.x; x[1] = p0.y; x[2] = p0.z; x[3] = p0.w;
+            x[4] = p1.x; x[5] = p1.y; x[6] = p1.z; x[7] = p1.w;
+            split3_store(op + kOpB, op + kOpB + kTcPartBytes, op + kOpB + 2 * kTcPartBytes, dst, x);
           }
         }
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(full_bf(bs));
+          mbar_arrive(full_op(bs));
           mbar_arrive(empty_st(fs));
+        }
+      }
+      if (energies && ok) {
+        // sum over the warp's rows (lanes with the same chunk), one FP64 add
+        // per column and warp
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          double v = (double)es[e] + (double)ec[e];
+          v += __shfl_xor_sync(0xffffffffu, v, 8);
+          v += __shfl_xor_sync(0xffffffffu, v, 16);
+          const int col = 64 * jb + 8 * cb + e;
+          if (lane < 8 && col < ti.kcols && col < kTcBN) atomicAdd(&ti.colE[col], v);
         }
       }
     }
   } else {
     // ------------------------------------------------------ epilogue
+    // Per stage: S = X (first stage) or S += X, kept in TMEM columns
+    // [kSCol0, kSCol0 + 128); at the tile's last stage S + X goes to global
+    // memory instead.  Row r of the tile lives in TMEM lane r.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    uint32_t tc = 0;
-    for (int tt = blockIdx.x; tt < n_tiles; tt += gridDim.x, ++tc) {
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int r = q * 32 + lane;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
       const TileInfo ti = tile_info(items, tiles[tt]);
-      const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
-      if (!warp_wait(tmem_full(acc), aph, abort_flag)) break;
-      tc_fence_after();
-      const int r = q * 32 + lane;
+      const int nkb = (ti.m + kTcBK - 1) / kTcBK;
       const bool vec = (ti.ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(ti.out) & 15) == 0;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const uint32_t xb = it & 1u;
+        if (!warp_wait(x_full(xb), (it >> 1) & 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const bool last = kb + 1 == nkb;
 #pragma unroll 1
-      for (int cc = 0; cc < kTcBN / 32; ++cc) {
-        const int nv = ti.validB - cc * 32;  // valid columns of this chunk (same in every lane)
-        if (nv <= 0) break;
-        float v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)kTcBN + cc * 32, v);
-        if (r < ti.validA) {
-          float* o = ti.out + (int64_t)r * ti.ldo + cc * 32;
-          if (vec) {
+        for (int cc = 0; cc < kTcBN / 32; ++cc) {
+          const int nv = ti.validB - cc * 32;  // valid columns of this chunk (same in every lane)
+          if (nv <= 0) break;
+          float v[32];
+          tmem_ld32(tmem_base + lane_off + kXCol0 + xb * (uint32_t)kTcBN + cc * 32, v);
+          if (kb > 0) {
+            float sacc[32];
+            tmem_ld32(tmem_base + lane_off + kSCol0 + cc * 32, sacc);
 #pragma unroll
-            for (int e4 = 0; e4 < 8; ++e4) {
-              const int e = 4 * e4;
-              if (e + 3 < nv) {
-                *reinterpret_cast<float4*>(o + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-              } else {
+            for (int e = 0; e < 32; ++e) v[e] += sacc[e];
+          }
+          if (!last) {
+            tmem_st32(tmem_base + lane_off + kSCol0 + cc * 32, v);
+          } else if (r < ti.validA) {
+            float* o = ti.out + (int64_t)r * ti.ldo + cc * 32;
+            if (vec) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  if (e + u < nv) o[e + u] = v[e + u];
+              for (int e4 = 0; e4 < 8; ++e4) {
+                const int e = 4 * e4;
+                if (e + 3 < nv) {
+                  *reinterpret_cast<float4*>(o + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                } else {
+#pragma unroll
+                  for (int u = 0; u < 4; ++u)
+                    if (e + u < nv) o[e + u] = v[e + u];
+                }
               }
-            }
-          } else {
+            } else {
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-              if (e < nv) o[e] = v[e];
+              for (int e = 0; e < 32; ++e)
+                if (e < nv) o[e] = v[e];
+            }
           }
         }
+        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(x_empty(xb));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tmem_empty(acc));
     }
   }
 
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(256)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
                  : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, kStatusWaitCap);
+}
+
+// ------------------------------------------------------- TMA tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool tc_tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out) {
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || (ld & 3) != 0 || cols < 1 || rows < 1)
+    return false;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kTcBox, (cuuint32_t)kTcBK};
+  cuuint32_t es[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles, int n_ctas,

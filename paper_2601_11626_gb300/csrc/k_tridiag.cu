@@ -131,6 +131,7 @@ __device__ __forceinline__ float core_gram(const CoreDesc& d, int n, int r, int 
     if (i < d.rt) return (i == l) ? d.sigma[i] * d.sigma[i] : 0.f;
     return d.sigma[l] * d.P[(int64_t)l * d.ldp + (i - d.rt)];
   }
+  if (i == l && d.colE) return (float)d.colE[l - d.rt];    // exact column energy
   return d.Gaa[(int64_t)(l - d.rt) * d.ldb + (i - d.rt)];  // upper part of A^T A
 }
 
@@ -457,10 +458,12 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     cb0[i] = core_gram(d, n, i, 0);
     cb1[i] = 0.f;
   }
-  // ||A||_F^2 = tr(A^T A) from the Gram's diagonal when no energy is given
+  // ||A||_F^2 = the sum of the column energies (else the Gram's diagonal)
+  // when no energy is given
   if (d.energy_add == nullptr) {
     double e = 0.0;
-    for (int i = tid; i < d.k; i += kThreads) e += (double)d.Gaa[(int64_t)i * d.ldb + i];
+    for (int i = tid; i < d.k; i += kThreads)
+      e += d.colE ? d.colE[i] : (double)d.Gaa[(int64_t)i * d.ldb + i];
     e = warp_sum_d(e);
     if (lane == 0) reinterpret_cast<double*>(red)[wid] = e;
   }
@@ -675,7 +678,10 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
   // 4. multisection bisection for the top r_new eigenvalues
   const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
   const float pivmin = 1.0e-30f * fmaxf(1.f, gem);
-  const float atol = 2.4e-7f * gnorm + 1e-30f;
+  // each eigenvalue to a few units in its own last place (the top-r sum
+  // then carries no bisection error beyond the Sturm counts' own), with an
+  // absolute floor far below the FP32 accuracy of the reduction
+  const float atol = 1e-12f * gnorm + 1e-30f;
   const int rq = d.r_new;
   int g = 1;
   while (g < 16 && g * 2 * rq <= kThreads) g *= 2;
@@ -693,7 +699,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     int it = 0;
     for (; it < kBisectMax; ++it) {
       // every lane of the warp runs the same number of iterations
-      const bool done = !active || stuck || !((b - a) > atol);
+      const bool done = !active || stuck || !((b - a) > fmaxf(atol, 2.4e-7f * fmaxf(fabsf(a), fabsf(b))));
       if (__all_sync(0xffffffffu, done)) break;
       const float step = (b - a) / (float)(g + 1);
       const float x = a + step * (float)(sub + 1);
@@ -734,6 +740,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       if (d.tail_paper_out) d.tail_paper_out[0] = paper;
       if (d.energy_out) d.energy_out[0] = energy_new;
       if (d.accept_out) d.accept_out[0] = (tail <= d.eps * d.eps * energy_new) ? 1 : 0;
+      if (d.refine) d.refine[0] = (tail < kRefineFrac * energy_new) ? 1 : 0;
     }
   }
 }

@@ -4,7 +4,7 @@
 // another allocator (a framework's caching allocator that owns the GPU), or
 // a latency-critical loop that must not pay cudaMalloc / cudaFree (which can
 // synchronise the device).  This entry point runs the same kernels as
-// csvd_score with CSVD_MIXED, with every intermediate (energy, P = U^T A,
+// csvd_score with CSVD_MIXED, with every intermediate (column energies, P = U^T A,
 // A^T A, the eigen core's global workspace, the kernel descriptors) placed
 // in one file-scope device array of fixed size that every GPU loading the
 // library holds until the process exits.
@@ -27,19 +27,21 @@ constexpr int kMaxRt = 128;
 constexpr int kMaxTiles = 4 + 10;  // P tiles (rt <= 128, k <= 512) + upper G tiles
 
 struct Descs {
+  CUtensorMap mapA;  // 64-byte aligned: first
+  CUtensorMap mapU;
   CoreDesc core;
-  EnergyDesc energy;
   TcItem item;
   TcTile tiles[kMaxTiles];
 };
 
 // Scratch layout (byte offsets, 256-byte aligned).
-constexpr size_t kOffEnergy = 0;
-constexpr size_t kOffDescs = 256;
-constexpr size_t kOffP = 4096;
+constexpr size_t kOffColE = 0;  // k column energies (FP64)
+constexpr size_t kOffDescs = size_t(kMaxK) * 8;
+constexpr size_t kOffP = kOffDescs + 4096;
 constexpr size_t kOffG = kOffP + size_t(kMaxRt) * kMaxK * 4;
 constexpr size_t kOffWork = kOffG + size_t(kMaxK) * kMaxK * 4;
 static_assert(sizeof(Descs) <= kOffP - kOffDescs, "descriptor region");
+static_assert(kOffDescs % 64 == 0, "tensor maps need 64-byte alignment");
 
 __global__ void write_descs_kernel(Descs d, Descs* dst) {
   if (threadIdx.x == 0) *dst = d;
@@ -69,42 +71,49 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
     return set_error(CSVD_ERR_SHAPE, "scratch limit: needs k <= 512 and rank <= 128");
   if (rt > 0 && (st->r & 3) != 0)
     return set_error(CSVD_ERR_SHAPE, "needs a state rank cap r divisible by 4");
+  const float* U = st->U[st->cur];
+  if (rt > 0 && (reinterpret_cast<uintptr_t>(U) & 15) != 0)
+    return set_error(CSVD_ERR_SHAPE, "needs a 16-byte aligned state basis");
   const int n = rt + k;
   const int cls = tridiag_class(n);
   const int64_t work_floats = tridiag_work_floats(cls, n, n);
   if ((size_t)kOffWork + (size_t)work_floats * 4 > kScratchBytes)
     return set_error(CSVD_ERR_SHAPE, "scratch limit exceeded");
+  // tensor maps of A and U (host-side encoding, no allocation)
+  Descs h;
+  std::memset(&h, 0, sizeof(h));
+  if (!tc_tensor_map(A->ptr, k, m, A->ld, &h.mapA))
+    return set_error(CSVD_ERR_SHAPE, "block cannot be described by a TMA tensor map");
+  if (rt > 0 && !tc_tensor_map(U, rt, m, st->r, &h.mapU))
+    return set_error(CSVD_ERR_SHAPE, "state basis cannot be described by a TMA tensor map");
 
   // set-up: the device address of the scratch array on the current device
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64)
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess || dev < 0 || dev >= 64)
     return set_error(CSVD_ERR_CUDA, "cudaGetDevice failed");
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ptr[dev]) {
       void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, csvd_noalloc_scratch);
-      if (e != cudaSuccess || !p)
+      e0 = cudaGetSymbolAddress(&p, csvd_noalloc_scratch);
+      if (e0 != cudaSuccess || !p)
         return set_error(CSVD_ERR_CUDA, "cudaGetSymbolAddress failed");
       g_ptr[dev] = p;
     }
     base = static_cast<unsigned char*>(g_ptr[dev]);
   }
   cudaStream_t s = st->stream;
-  double* energy = reinterpret_cast<double*>(base + kOffEnergy);
+  double* colE = reinterpret_cast<double*>(base + kOffColE);
   Descs* ddesc = reinterpret_cast<Descs*>(base + kOffDescs);
   float* P = reinterpret_cast<float*>(base + kOffP);
   float* G = reinterpret_cast<float*>(base + kOffG);
   float* work = reinterpret_cast<float*>(base + kOffWork);
 
-  Descs h;
-  std::memset(&h, 0, sizeof(h));
-  h.energy = EnergyDesc{A->ptr, A->ld, (int)m, k, 0, 0, energy};
   const int kld = (k + 3) & ~3;  // 16-byte rows for the Gram kernel's stores
-  h.item = TcItem{reinterpret_cast<const float*>(A->ptr), A->ld, st->U[st->cur], st->r, (int)m, k,
-                  rt, 0, P, kld, G, kld};
+  h.item = TcItem{reinterpret_cast<const float*>(A->ptr), A->ld, U, st->r, (int)m, k, rt, 0,
+                  P, kld, G, kld, colE, &ddesc->mapA, rt > 0 ? &ddesc->mapU : &ddesc->mapA};
   int nt = 0;
   for (int r0 = 0; r0 < rt; r0 += kTcBM)
     for (int c0 = 0; c0 < k; c0 += kTcBN) h.tiles[nt++] = TcTile{0, 0, r0, c0};
@@ -114,10 +123,11 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   c.P = rt > 0 ? P : nullptr;
   c.ldp = kld;
   c.Gaa = G;
+  c.colE = colE;
   c.ldb = kld;
   c.sigma = st->sigma;
   c.scal = st->scal;
-  c.energy_add = energy;
+  c.energy_add = nullptr;  // the sum of the column energies
   c.work = work_floats > 0 ? work : nullptr;
   c.ldwork = n;
   c.sigma_out = sigma_out;
@@ -130,14 +140,13 @@ extern "C" csvd_status csvd_score_one_noalloc(csvd_state st, const csvd_block* A
   c.kp = (int)std::min<int64_t>(k, m - rt);
   c.r_new = std::min(st->r, rt + c.kp);
 
-  // energies start at zero; descriptors are written by a kernel (no host staging)
-  e = cudaMemsetAsync(energy, 0, sizeof(double), s);
+  // column energies start at zero; descriptors are written by a kernel (no
+  // host staging)
+  cudaError_t e = cudaMemsetAsync(colE, 0, sizeof(double) * (size_t)k, s);
   if (e == cudaSuccess) {
     write_descs_kernel<<<1, 32, 0, s>>>(h, ddesc);
     e = cudaGetLastError();
   }
-  const int chunks = (int)std::min<int64_t>(64, (m * k + 8191) / 8192);
-  if (e == cudaSuccess) e = launch_energy(&ddesc->energy, 1, chunks, s);
   if (e == cudaSuccess)
     e = launch_tc_gram(&ddesc->item, ddesc->tiles, nt, device_sm_count(), st->status, s);
   if (e == cudaSuccess) e = launch_core_tridiag(cls, &ddesc->core, 1, n, st->status, s);

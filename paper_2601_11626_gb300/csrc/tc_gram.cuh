@@ -1,6 +1,8 @@
 // Tensor-core Gram / projection kernel of the mixed merge evaluation.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace csvd {
@@ -17,8 +19,9 @@ struct TcItem {
   int64_t ldp;
   float* G;      // k x k, row-major ldg:   G = A^T A (tiles on and above the diagonal)
   int64_t ldg;   // P and G take 16-byte stores when ldp, ldg % 4 == 0 and 16-byte aligned
-  const void* mapA;  // optional 2-D TMA tensor map of A (box 32 rows x 128 cols), device memory
-  const void* mapU;  // optional tensor map of U (same box); both or neither
+  double* colE;  // k column energies sum_i A_ic^2, accumulated (zeroed before the launch)
+  const void* mapA;  // 2-D TMA tensor map of A (tc_tensor_map), device memory
+  const void* mapU;  // tensor map of U (any valid map when rt == 0)
 };
 
 // A 128 x 128 output tile: kind 0 -> rows from U (P), kind 1 -> rows from A (G).
@@ -26,15 +29,26 @@ struct TcTile {
   int item, kind, row0, col0;
 };
 
-// Two rings: f32 staging slots filled by TMA (deep, to cover the load
-// latency) and split bf16 operand slots read by the MMAs.
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32;
-constexpr int kTcStagesF = 5, kTcStagesB = 2;
-constexpr int kTcConvWarps = 16;  // split warps: one 8-deep chunk of one row each
+// Output tile 128 x 128.  A staging slot holds kTcBK rows of both operands
+// as TMA boxes of kTcBK rows x kTcBox f32 columns (128 bytes, 128-byte
+// swizzle), four boxes per 128-column panel; an operand slot holds the
+// three bf16 parts of both operands in the MN-major 128-byte-swizzled UMMA
+// layout (two 64-column atoms of kTcBK rows per part).
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcBox = 32;
+constexpr int kTcStagesF = 3, kTcStagesB = 2;
+constexpr int kTcConvWarps = 8;  // warps splitting f32 into bf16 parts
 constexpr int kTcThreads = (2 + kTcConvWarps + 4) * 32;
-constexpr int kTcStageF = 2 * kTcBK * kTcBM * 4;  // 32 KB: A and B rows, f32
-constexpr int kTcStageB = 4 * kTcBM * kTcBK * 2;  // 32 KB: A hi/lo, B hi/lo, bf16
+constexpr int kTcBoxBytes = kTcBK * kTcBox * 4;                 // 4 KB
+constexpr int kTcStageF = 2 * (kTcBM / kTcBox) * kTcBoxBytes;   // 32 KB: A and B, f32
+constexpr int kTcPartBytes = kTcBK * kTcBM * 2;                 // 8 KB: one bf16 part
+constexpr int kTcStageB = 6 * kTcPartBytes;                     // 48 KB: 3 parts x 2 operands
 constexpr int kTcSmemBytes = kTcStagesF * kTcStageF + kTcStagesB * kTcStageB + 2048;
+
+// Encodes the tensor map the kernel expects for a row-major f32 matrix
+// (rows x cols, leading dimension ld floats): box kTcBK rows x kTcBox
+// columns, 128-byte swizzle, zero fill outside the matrix.  False when the
+// driver entry point is unavailable or rejects the matrix (alignment).
+bool tc_tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out);
 
 cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles,
                            int n_ctas, int* d_status, cudaStream_t s);

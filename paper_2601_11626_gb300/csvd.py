@@ -31,7 +31,18 @@ class Status(enum.IntEnum):
     ERR_UNIMPLEMENTED = 7
 
 
-PLAIN, MIXED = 0, 1
+PLAIN, MIXED, GRAM_FP32 = 0, 1, 2
+PRECISION = {"plain": PLAIN, "mixed": MIXED, "gram_fp32": GRAM_FP32}
+
+
+def _prec(precision: str) -> int:
+    """C enum of a precision name: "plain" (residual + Jacobi, FP32 SIMT),
+    "mixed" (tensor-core Gram route) or "gram_fp32" (the Gram route with
+    FP32 SIMT products)."""
+    try:
+        return PRECISION[precision]
+    except KeyError:
+        raise ValueError(f"precision must be one of {sorted(PRECISION)}, not {precision!r}")
 ALGO = {"weyl": 1, "residual": 2, "approx": 3}
 SORT = {"frobenius": 0, "residual": 1}
 F32, BF16 = 0, 1
@@ -161,7 +172,7 @@ class IncrSVD:
         self.m, self.r = m, r
         self.stream = stream or torch.cuda.current_stream()
         h = C.c_void_p()
-        _check(self._lib.csvd_incr_init(C.byref(h), m, r, MIXED if precision == "mixed" else PLAIN,
+        _check(self._lib.csvd_incr_init(C.byref(h), m, r, _prec(precision),
                                         _stream(self.stream)))
         self._h = h
         self._keep = []
@@ -263,7 +274,7 @@ class Stream:
         self.stream = stream or torch.cuda.current_stream()
         h = C.c_void_p()
         _check(self._lib.csvd_stream_init(C.byref(h), m, r, self.eps,
-                                          MIXED if precision == "mixed" else PLAIN,
+                                          _prec(precision),
                                           _stream(self.stream)))
         self._h = h
         self.labels = []
@@ -311,7 +322,7 @@ class ScoreBatch:
         self.states = states
         self.n = len(cands)
         self.eps = float(eps)
-        self.precision = MIXED if precision == "mixed" else PLAIN
+        self.precision = _prec(precision)
         self._st = (C.c_void_p * len(states))(*[s.handle.value for s in states])
         self._cs = (C.c_int32 * self.n)(*[int(x) for x in cand_state])
         self._cb = _blocks(cands, states[0].m)
@@ -429,7 +440,7 @@ def cluster(blocks, r, eps, algo="approx", sort_mode="frobenius", precision="pla
     en = (C.c_double * n)()
     ratio = C.c_double()
     _check(lib().csvd_cluster(_blocks(blocks), n, m, r, float(eps), ALGO[algo], SORT[sort_mode],
-                              MIXED if precision == "mixed" else PLAIN, _stream(), labels, est,
+                              _prec(precision), _stream(), labels, est,
                               en, C.byref(ratio)))
     lab = list(labels)
     k = max(lab) + 1

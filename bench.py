@@ -137,6 +137,155 @@ def _work_per_candidate(m, rt, k):
     )
 
 
+def _tc_issued_flops(m, rt, k, tile=128, kstep=32, parts=6):
+    """bf16 tensor-core flops the Gram kernel issues for one candidate: every
+    128 x 128 output tile (P tiles over U's rt columns, the upper tiles of
+    A^T A) runs M = 128, N = its valid columns rounded up to 16, over the m
+    rows rounded up to the 32-row stage, six MMAs per product."""
+    mp = -(-m // kstep) * kstep
+    f = 0.0
+    for c0 in range(0, k, tile):
+        nfit = min(tile, -(-(k - c0) // 16) * 16)
+        rows = (-(-rt // tile)) + (c0 // tile + 1)  # P row tiles + G row tiles at or above c0
+        f += rows * 2.0 * tile * nfit * mp * parts
+    return f
+
+
+def _time_form(csvd, states, cand_state, cands, eps, form, steps, stream, ref):
+    """CUDA-event time of ``steps`` csvd_score calls in one form after one
+    untimed call; with ``ref`` (a ScoreBatch of the same candidates), the
+    largest relative difference of E~ and whether the accept flags agree."""
+    import torch
+    b = csvd.ScoreBatch(states, cand_state, cands, eps, form)
+    b.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.run()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"value": len(cands) / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "steps": steps}
+    if ref is not None:
+        out["max_tail_rel_diff_vs_mixed"] = float(((b.tail.sqrt() - ref.tail.sqrt()).abs()
+                                                   / ref.tail.sqrt().clamp_min(1e-300)).max())
+        out["accept_agree"] = bool((b.accept == ref.accept).all())
+    del b
+    return out
+
+
+def rank_legs(csvd, synth, ranks, rank, steps):
+    """The batched-scoring workload at other state ranks: mixed form against
+    the same-algorithm FP32 comparator, device-resident inputs."""
+    import torch
+    out = {}
+    for r in ranks:
+        w = synth.scoring_c4(r=r, seed=rank, device="cuda")
+        states = []
+        for blocks in w["states"]:
+            st = csvd.IncrSVD(w["m"], r)
+            for b in blocks:
+                st.append(b)
+            states.append(st)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        mixed = _time_form(csvd, states, w["cand_state"], w["candidates"], w["eps"], "mixed",
+                           steps, stream, None)
+        ref = csvd.ScoreBatch(states, w["cand_state"], w["candidates"], w["eps"], "mixed").run()
+        fp32 = _time_form(csvd, states, w["cand_state"], w["candidates"], w["eps"], "gram_fp32",
+                          steps, stream, ref)
+        out[f"r{r}"] = {"mixed": mixed["value"], "mixed_ms_per_step": mixed["ms_per_step"],
+                        "plain_fp32": fp32["value"], "plain_fp32_ms_per_step": fp32["ms_per_step"],
+                        "speedup": mixed["value"] / fp32["value"],
+                        "max_tail_rel_diff": fp32["max_tail_rel_diff_vs_mixed"],
+                        "accept_agree": fp32["accept_agree"], "steps": steps,
+                        "n_candidates": len(w["candidates"])}
+        del ref
+        for st in states:
+            st.close()
+        del w, states
+        torch.cuda.empty_cache()
+    return out
+
+
+def c2_leg(csvd, synth, steps, oracle_samples):
+    """The mid-size recipe (256 blocks 1024 x 128, 16 latent subspaces, r = 64)
+    at eps in {0.02, 0.05, 0.1}: 16 states (blocks c, c + 16, c + 32 of
+    subspace c), every other block scored against its own subspace's state
+    and the next one's; mixed form against the same-algorithm FP32
+    comparator and the residual + Jacobi form; accept counts per eps and
+    the oracle's E~ on a sample that includes same-subspace merges."""
+    import numpy as np
+    import torch
+    from oracle import incremental as oinc
+    col = synth.mid_c2(device="cuda")
+    m, r = col.m, col.meta["r"]
+    groups = [[c, c + 16, c + 32] for c in range(16)]
+    states = []
+    for g in groups:
+        st = csvd.IncrSVD(m, r)
+        for j in g:
+            st.append(col.blocks[j])
+        states.append(st)
+    rest = [j for j in range(48, len(col.blocks))]
+    cands, cs = [], []
+    for j in rest:
+        c = j % 16
+        cands += [col.blocks[j], col.blocks[j]]
+        cs += [c, (c + 1) % 16]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{len(states)} states (3 blocks each) x {len(cands)} evaluations, m={m}, "
+                       f"k=128, r={r}", "n_candidates": len(cands)}
+    ref = csvd.ScoreBatch(states, cs, cands, 0.05, "mixed").run()
+    forms = {}
+    for form in ("mixed", "gram_fp32", "plain"):
+        forms[form] = _time_form(csvd, states, cs, cands, 0.05, form, steps, stream,
+                                 None if form == "mixed" else ref)
+    out["mixed"] = forms["mixed"]["value"]
+    out["plain_fp32"] = forms["gram_fp32"]["value"]
+    out["plain_fp32_jacobi"] = forms["plain"]["value"]
+    out["speedup"] = forms["mixed"]["value"] / forms["gram_fp32"]["value"]
+    out["speedup_vs_jacobi"] = forms["mixed"]["value"] / forms["plain"]["value"]
+    tails = ref.tail.cpu().numpy()
+    energies = []
+    per_eps = {}
+    # oracle sample: same-subspace merges (small tails) and cross-subspace ones
+    rng = np.random.default_rng(5)
+    idx = sorted(set([int(i) for i in rng.choice(len(cands), oracle_samples, replace=False)] +
+                     list(range(0, 2 * oracle_samples, 2))))
+    cache, worst, rels = {}, 0.0, {}
+    for i in idx:
+        s_ = cs[i]
+        if s_ not in cache:
+            st = states[s_]
+            te = st.tail_error()
+            cache[s_] = oinc.IncrementalSVD(m, r, st.basis().double().cpu().numpy(),
+                                            st.sigma().astype(np.float64), te["energy"],
+                                            te["tail_sq"])
+        s_o, t_o, a_o, nxt = cache[s_].evaluate(cands[i].cpu(), 0.05)
+        worst = max(worst, abs(math.sqrt(tails[i]) - math.sqrt(nxt[3])) / math.sqrt(nxt[3]))
+        rels[i] = math.sqrt(nxt[3] / nxt[2])
+    for eps in (0.02, 0.05, 0.1):
+        b = csvd.ScoreBatch(states, cs, cands, eps, "mixed").run()
+        acc = b.accept.cpu().numpy()
+        agree = sum(int(bool(acc[i]) == (rels[i] <= eps)) for i in idx
+                    if abs(rels[i] - eps) > 1e-3 * eps)
+        boundary = [i for i in idx if abs(rels[i] - eps) <= 1e-3 * eps]
+        per_eps[str(eps)] = {"accepted": int(acc.sum()), "sampled_accept_agree": agree,
+                             "sampled_boundary": boundary}
+        del b
+    out["per_eps"] = per_eps
+    out["sampled"] = len(idx)
+    out["sampled_rel_tail_range"] = [min(rels.values()), max(rels.values())]
+    out["max_tail_rel_err"] = worst
+    del ref
+    for st in states:
+        st.close()
+    return out
+
+
 def cpu_baseline(w, eps, budget_s=15.0, max_evals=64):
     """Oracle (FP64 numpy) merge evaluations on a bounded sample of the same
     workload: the states of the first candidates are rebuilt on the CPU
@@ -468,10 +617,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--r", type=int, default=64)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain", "gram_fp32"])
     ap.add_argument("--n-states", type=int, default=64)
     ap.add_argument("--per-state", type=int, default=64)
-    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--jacobi-candidates", type=int, default=512,
+                    help="candidates timed in the residual + Jacobi form (0: skip)")
+    ap.add_argument("--no-legs", dest="legs", action="store_false",
+                    help="skip the other-rank and mid-size legs")
+    ap.add_argument("--leg-ranks", default="32,128")
+    ap.add_argument("--leg-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=20,
                     help="end-to-end steps; the first copy cannot overlap a step, so more "
                          "steps weigh the pipeline fill less")
@@ -520,6 +675,9 @@ def main():
     ranks = [s.rank for s in states]
     cands = w["candidates"]
     n = len(cands)
+    k_mean = sum(c.shape[1] for c in cands) / n
+    pool_bytes = w["pools"][1].numel() * 4
+    n_states = len(states)
     batch = csvd.ScoreBatch(states, w["cand_state"], cands, eps, args.precision)
 
     def barrier():
@@ -573,26 +731,38 @@ def main():
                 "peak_note": f"{peak_src} copy bandwidth"}
     roof["kernels"] = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(x[1] for x in prof.values())}
                        for k, v in prof.items()}
+    if "tc_gram" in groups:
+        g_ms = groups["tc_gram"][1]
+        issued = sum(_tc_issued_flops(m, ranks[w["cand_state"][i]], cands[i].shape[1])
+                     for i in range(n))
+        roof["tc_gram"] = {
+            "ms_per_step": g_ms / args.steps,
+            "hbm_gbs": gram_bytes * args.steps / (g_ms / 1000.0) / 1e9,
+            "hbm_frac": gram_bytes * args.steps / (g_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+            "tensor_tflops": issued * args.steps / (g_ms / 1000.0) / 1e12,
+            "tensor_frac": issued * args.steps / (g_ms / 1000.0) / 1e12 / peaks["bf16_tflops"],
+            "note": f"algorithmic bytes (A once, U once per candidate) over the kernel's CUDA-event "
+                    f"time; issued bf16 MMA flops (six per product, padded tiles) against the "
+                    f"{peak_src} bf16 peak"}
 
-    # plain FP32 form of the same evaluations
+    # the plain FP32 comparator of the metric: the same Gram route with FP32
+    # SIMT products, on every candidate; and the residual + Jacobi route (the
+    # step as Lemma 1 states it) on a bounded subset
     plain = None
     if args.plain_steps > 0 and args.precision == "mixed":
-        pb = csvd.ScoreBatch(states, w["cand_state"], cands, eps, "plain")
-        pb.run()
-        torch.cuda.synchronize()
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(args.plain_steps):
-            pb.run()
-        p1.record(stream)
-        p1.synchronize()
-        pms = p0.elapsed_time(p1) / args.plain_steps
-        plain = {"value": world * n / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
-                 "steps": args.plain_steps,
-                 "max_tail_rel_diff_vs_mixed": float(((pb.tail.sqrt() - batch.tail.sqrt()).abs()
-                                                      / batch.tail.sqrt().clamp_min(1e-300)).max()),
-                 "accept_agree": bool((pb.accept == batch.accept).all())}
-        del pb
+        plain = _time_form(csvd, states, w["cand_state"], cands, eps, "gram_fp32", args.plain_steps,
+                           stream, batch)
+        plain["form"] = "Gram route with FP32 SIMT products (same algorithm as the mixed form)"
+        plain["value"] *= world
+        plain["speedup_of_mixed"] = value / plain["value"]
+    jacobi = None
+    if args.jacobi_candidates > 0 and args.precision == "mixed":
+        sub = min(n, args.jacobi_candidates)
+        jacobi = _time_form(csvd, states, w["cand_state"][:sub], cands[:sub], eps, "plain",
+                            args.plain_steps, stream, None)
+        jacobi["form"] = "residual, Householder QR and one-sided Jacobi on K, FP32 SIMT"
+        jacobi["candidates"] = sub
+        jacobi["value"] *= world
 
     # end to end through the public API: every step copies its inputs from
     # pinned host memory and reads its results back; the copy of step i runs
@@ -699,22 +869,34 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, eps)
 
+    # other state ranks and the mid-size recipe (free the main workload first)
+    legs = None
+    if args.legs and args.precision == "mixed":
+        ranks_ = [int(x) for x in args.leg_ranks.split(",") if x]
+        del batch
+        for st in states:
+            st.close()
+        states = []
+        del w, cands
+        torch.cuda.empty_cache()
+        legs = {"ranks": rank_legs(csvd, synth, ranks_, rank, args.leg_steps),
+                "c2": c2_leg(csvd, synth, max(args.leg_steps, 3), 12)}
+
     if rank == 0:
-        ks = [c.shape[1] for c in cands]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": f"batched uneven merge scoring: {len(states)} states x {args.per_state} "
+                "workload": f"batched uneven merge scoring: {n_states} states x {args.per_state} "
                             f"candidates per GPU, m={m}, k~U[16,512], r={r}",
-                "m": m, "r": r, "n_candidates": n, "k_mean": sum(ks) / n, "k_range": [16, 512],
+                "m": m, "r": r, "n_candidates": n, "k_mean": k_mean, "k_range": [16, 512],
                 "precision_form": args.precision, "eps": eps,
-                "l2": "inputs (%.1f GB) larger than L2, no flush" % (
-                    w["pools"][1].numel() * 4 / 1e9),
+                "l2": "inputs (%.1f GB) larger than L2, no flush" % (pool_bytes / 1e9),
                 "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
-            "plain_fp32": plain, "parity": parity, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "gpu_launches": launches,
+            "plain_fp32": plain, "plain_fp32_jacobi": jacobi, "parity": parity, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": launches, "legs": legs,
         }
         print(json.dumps(line), flush=True)
     for st in states:

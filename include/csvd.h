@@ -284,8 +284,13 @@ csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m, vo
  * intermediate lives in one file-scope device array of 4 MiB that each GPU
  * loading the library holds until the process exits; no call allocates.
  * Limits: f32 block with 16-byte aligned rows (ptr % 16 == 0, ld % 4 == 0),
- * k <= 512, state rank r_t <= 128 and rank cap r divisible by 4; larger
- * sizes return CSVD_ERR_SHAPE.  Outputs are device pointers as in
+ * k <= 512, state rank r_t <= 128 and rank cap r divisible by 4, state
+ * basis 16-byte aligned; larger sizes (or a basis or block that no TMA
+ * tensor map can describe) return CSVD_ERR_SHAPE, a misaligned block
+ * CSVD_ERR_ARG, before any launch.  The products always run on the tensor
+ * cores (the CSVD_GRAM environment switch does not apply), and there is no
+ * FP64 re-solve: a tail below 2e-3 of the merged energy keeps the FP32
+ * core's absolute accuracy of a few u ||M||^2.  Outputs are device pointers as in
  * csvd_score (sigma_out: at least min(r, r_t + k) floats; tail_paper_out
  * and accept_out may be NULL).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current,

@@ -9,8 +9,9 @@
 //     #{lambda < x} = #{j : d_j < x} + [f(x) < 0],
 //     f(x) = alpha - x - sum_j z_j^2 / (d_j - x)   (the secular function),
 // an exact O(r_t) count.  The top r_new eigenvalues give sigma~_j =
-// sqrt(lambda_j) (Cor. 3) and the tail follows from the trace, tr(G) - sum
-// of the top, summed as double-float pairs and finished in FP64.
+// sqrt(lambda_j) (Cor. 3); when the merge truncates (r_new = r_t), the one
+// discarded eigenvalue is found the same way and is the step's tail, each
+// root to a few units in its own last place.
 //
 // diag(d) is the leading principal block of G, so (Cauchy interlacing) with
 // s non-increasing the q-th largest eigenvalue lies in [d_q, d_{q-1}] (ends
@@ -275,19 +276,23 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   }
   __syncthreads();
 
-  // 3. one task per (candidate, eigenvalue)
-  const int ntask = cnt * rq;
+  // 3. one task per (candidate, eigenvalue): the top rq and, when the merge
+  //    truncates, the discarded one (n - rq <= 1 for one column)
+  const int nroot = n;
+  const int ntask = cnt * nroot;
   int capped = 0;
   if (sorted) {
     // bracketed rational-model iteration, one thread per task
     for (int t0 = 0; t0 < ntask; t0 += kArrowThreads) {  // uniform trip count
       const int t = t0 + tid;
       const bool active = t < ntask;
-      const int item = active ? t / rq : 0, q = active ? t % rq : 0;
+      const int item = active ? t / nroot : 0, q = active ? t % nroot : 0;
       const float glo = s_lo[item], ghi = s_hi[item];
       const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
       const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
-      const float atol = 2.4e-7f * gnorm + 1e-30f;
+      // each root to a few units in its own last place (the discarded one
+      // is the tail itself), with an absolute floor far below FP32 accuracy
+      const float afloor = 1e-12f * gnorm + 1e-30f;
       const float alpha = (float)s_alpha[item];
       const float2* dz = s_dz[item];
       const bool has_l = q < rt, has_r = q > 0;
@@ -295,6 +300,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
       float a = has_l ? fmaxf(glo, dl) : glo, b = has_r ? fminf(ghi, dr) : ghi;
       if (a > b) a = b;
       float x = 0.5f * (a + b), lam = x;
+      float atol = fmaxf(afloor, 2.4e-7f * fmaxf(fabsf(a), fabsf(b)));
       bool done = !active || !((b - a) > atol);
       bool probed = false;
       int it = 0;
@@ -311,6 +317,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
           D = fmaf(tt, inv, D);
         }
         if (f < 0.f) b = x; else a = x;  // x above the root iff f(x) < 0
+        atol = fmaxf(afloor, 2.4e-7f * fmaxf(fabsf(a), fabsf(b)));
         if (!((b - a) > atol)) {
           done = true;
           lam = x;
@@ -371,18 +378,19 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
     for (int t0 = 0; t0 < ntask; t0 += ngroups) {  // uniform trip count across the block
       const int t = t0 + grp;
       const bool active = t < ntask;
-      const int item = active ? t / rq : 0, q = active ? t % rq : 0;
+      const int item = active ? t / nroot : 0, q = active ? t % nroot : 0;
       const int target = n - 1 - q;  // ascending index of the q-th largest
       const float glo = s_lo[item], ghi = s_hi[item];
       const float gnorm = fmaxf(fabsf(glo), fabsf(ghi));
       const float pivmin = 1.0e-30f * fmaxf(1.f, gnorm);
-      const float atol = 2.4e-7f * gnorm + 1e-30f;
+      const float afloor = 1e-12f * gnorm + 1e-30f;
       const float alpha = (float)s_alpha[item];
       const float* z2 = s_z2[item];
       float a = glo, b = ghi;
       bool stuck = false;
       int it = 0;
       for (; it < kArrowBisectMax; ++it) {
+        const float atol = fmaxf(afloor, 2.4e-7f * fmaxf(fabsf(a), fabsf(b)));
         const bool done = !active || stuck || !((b - a) > atol);
         if (__all_sync(0xffffffffu, done)) break;
         const float step = (b - a) / (float)(g + 1);
@@ -408,24 +416,24 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
   if (capped) atomicOr(status, kStatusBisectCap);
   __syncthreads();
 
-  // 4. FP64 epilogue (warp g <-> candidate g): sigma~, tail from the trace,
-  //    energy, accept flag
+  // 4. FP64 epilogue (warp g <-> candidate g): sigma~, the tail as the
+  //    discarded eigenvalue itself (no difference of sums as large as
+  //    ||M||^2), energy, accept flag
   if (wid < cnt) {
     const double alpha_d = s_alpha[wid];
     float* sig_out = V.sigma_out[wid];
-    float ts = 0.f, tc = 0.f, ds = 0.f, dc = 0.f;  // double-float sums of the top and of d
+    float ts = 0.f, tc = 0.f;  // double-float sum of the top
     for (int q = lane; q < rq; q += 32) {
       arrow_ff_add(ts, tc, s_lam[wid][q], 0.f);
       sig_out[q] = sqrtf(fmaxf(s_lam[wid][q], 0.f));
     }
-    for (int j = lane; j < rt; j += 32) arrow_ff_add(ds, dc, s_d[j], 0.f);
     arrow_ff_warp_sum(ts, tc);
-    arrow_ff_warp_sum(ds, dc);
     if (lane == 0) {
       const double top = (double)ts + (double)tc;
-      const double tr = (double)ds + (double)dc + alpha_d;
+      double disc = 0.0;
+      for (int q = rq; q < nroot; ++q) disc += (double)fmaxf(s_lam[wid][q], 0.f);
       const double energy_new = V.scal[0] + alpha_d;
-      double tail = V.scal[1] + (tr - top);
+      double tail = V.scal[1] + disc;
       if (tail < 0.0) tail = 0.0;
       double paper = energy_new - top;
       if (paper < 0.0) paper = 0.0;

@@ -71,10 +71,17 @@ def test_stream_matches_oracle(csvd, eps, precision):
         assert nb == want["labels"].count(c)
         te = st.tail_error()
         assert te["energy"] == pytest.approx(ost.energy, rel=1e-5)
-        g, w = math.sqrt(max(te["tail_sq"], 0.0)), math.sqrt(ost.discarded)
-        assert abs(g - w) <= 1e-3 * w + math.sqrt(1e-6 * ost.energy), (c, g, w)
+        # the cluster's state went through several appends (the plain FP32
+        # step), each adding FP32 rounding of the basis: E~ within 1e-4
+        # relative plus 8 u ||M||^2 on E~^2
+        g, w = max(te["tail_sq"], 0.0), ost.discarded
+        assert abs(g - w) <= 2e-4 * w + 8 * 2.0 ** -24 * ost.energy, (c, g, w)
         sig = st.sigma()
-        np.testing.assert_allclose(sig, ost.s[:len(sig)], rtol=1e-4, atol=2e-6 * ost.s[0])
+        sref = ost.s[:len(sig)]
+        ok = np.abs(sig - sref) <= 1e-5 * sref + 2e-6 * sref[0]
+        ok |= np.abs(sig.astype(np.float64) ** 2 - sref ** 2) <= 2e-5 * sref ** 2 + \
+            8 * 2.0 ** -24 * sref[0] ** 2
+        assert np.all(ok), (c, sig, sref)
         assert st.basis().shape == (m, len(sig))
     s.close()
 

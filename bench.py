@@ -449,6 +449,13 @@ def run_k1(args, world, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # launch-class edges of the eigen core for this batch (untimed)
+    tuning = None
+    if args.tune and args.precision != "plain":
+        from paper_2601_11626_gb300 import tune
+        tuning = tune.autotune(batch, [ranks[w["cand_state"][i]] + cands[i].shape[1]
+                                       for i in range(n)], m, ranks, steps=2)
+        tuning["edges"] = list(tuning["edges"])
     for _ in range(args.warmup):
         batch.run()
     barrier()
@@ -627,6 +634,8 @@ def main():
                     help="skip the other-rank and mid-size legs")
     ap.add_argument("--leg-ranks", default="32,128")
     ap.add_argument("--leg-steps", type=int, default=3)
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="keep the hand-set launch classes of the eigen core")
     ap.add_argument("--e2e-steps", type=int, default=20,
                     help="end-to-end steps; the first copy cannot overlap a step, so more "
                          "steps weigh the pipeline fill less")
@@ -685,6 +694,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # launch-class edges of the eigen core for this batch (untimed)
+    tuning = None
+    if args.tune and args.precision != "plain":
+        from paper_2601_11626_gb300 import tune
+        tuning = tune.autotune(batch, [ranks[w["cand_state"][i]] + cands[i].shape[1]
+                                       for i in range(n)], m, ranks, steps=2)
+        tuning["edges"] = list(tuning["edges"])
     for _ in range(args.warmup):
         batch.run()
     barrier()
@@ -896,7 +912,7 @@ def main():
                 "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
             "plain_fp32": plain, "plain_fp32_jacobi": jacobi, "parity": parity, "e2e": e2e,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-            "gpu_launches": launches, "legs": legs,
+            "gpu_launches": launches, "legs": legs, "tuning": tuning,
         }
         print(json.dumps(line), flush=True)
     for st in states:

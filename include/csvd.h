@@ -302,6 +302,31 @@ csvd_status csvd_score_one_noalloc(csvd_state s, const csvd_block* A, double eps
                                    double* tail_sq_out, double* tail_paper_out,
                                    uint8_t* accept_out);
 
+/* Tunable launch configuration of the mixed form's eigen core (set by the
+ * autotuner, paper_2601_11626_gb300/tune.py; the paper has no
+ * counterpart).  Cores of size n = r_t + k <= edge_small run in the small
+ * launch class (4 warps, 4 CTAs per SM), n <= edge_medium in the medium one
+ * (8 warps, 2 CTAs per SM), larger ones one CTA of 16 warps per SM.
+ * Ranges: 64 <= edge_small <= 288, edge_small < edge_medium <= 480;
+ * (-1, -1) restores the defaults (192, 320); out-of-range values return
+ * CSVD_ERR_ARG and change nothing.  Process-wide; results change only at
+ * the level of FP32 rounding (the order of the core's sums). */
+csvd_status csvd_tune_set(int32_t edge_small, int32_t edge_medium);
+csvd_status csvd_tune_get(int32_t* edge_small, int32_t* edge_medium);
+
+/* Failure-path test hook (the paper has no counterpart).  Sets, for the
+ * current device, the sweep cap of the one-sided Jacobi core
+ * (jacobi_sweeps, default 40), the iteration cap of every bisection and
+ * secular-root iteration (solver_iters, default 64; 128 for the FP64
+ * re-solve) and the limit of the tensor-core Gram kernel's pipeline waits
+ * in ns of device time (wait_ns, default 2e9; the drains after an abort
+ * keep the default).  A negative value restores the default.  A cap that is
+ * hit surfaces as CSVD_ERR_NOT_CONVERGED, a wait that gives up as
+ * CSVD_ERR_TIMEOUT, both at the next synchronising call on the state whose
+ * status word the launch used; results of that call are not meaningful.
+ * Not thread-safe against concurrent launches. */
+csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns);
+
 /* Launch tracing.  csvd_launch_count: kernels launched by this library so
  * far in the process.  csvd_profile(1) clears and starts recording a pair of
  * CUDA events on the launch stream around every kernel launch, csvd_profile(0)

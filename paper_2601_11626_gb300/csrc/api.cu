@@ -883,6 +883,31 @@ extern "C" {
 const char* csvd_last_error(void) { return g_err.c_str(); }
 const char* csvd_version(void) { return "csvd 0.1 (sm_103a)"; }
 
+csvd_status csvd_tune_set(int32_t edge_small, int32_t edge_medium) {
+  if (!tridiag_set_edges(edge_small, edge_medium))
+    return fail(CSVD_ERR_ARG, "launch-class edges out of range");
+  return CSVD_OK;
+}
+
+csvd_status csvd_tune_get(int32_t* edge_small, int32_t* edge_medium) {
+  if (!edge_small || !edge_medium) return fail(CSVD_ERR_ARG, "NULL argument");
+  int a, b;
+  tridiag_get_edges(&a, &b);
+  *edge_small = a;
+  *edge_medium = b;
+  return CSVD_OK;
+}
+
+csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns) {
+  cudaError_t e = jacobi_set_cap(jacobi_sweeps);
+  if (e == cudaSuccess) e = tridiag_set_bisect_cap(solver_iters);
+  if (e == cudaSuccess) e = refine64_set_bisect_cap(solver_iters);
+  if (e == cudaSuccess) e = arrow_set_cap(solver_iters);
+  if (e == cudaSuccess) e = tc_set_wait_ns(wait_ns);
+  if (e != cudaSuccess) return fail(CSVD_ERR_CUDA, cudaGetErrorString(e));
+  return CSVD_OK;
+}
+
 csvd_status csvd_set_allocator(csvd_alloc_fn alloc, csvd_free_fn free_, void* ctx) {
   if ((alloc == nullptr) != (free_ == nullptr))
     return fail(CSVD_ERR_ARG, "allocator and free must both be set or both be NULL");

@@ -201,6 +201,13 @@ int jacobi_scratch_floats(int nc);
 // that launch (nonzero only for the largest cores).
 constexpr int kTriLargeSmemBytes = 227 * 1024 - 1024;
 int tridiag_class(int n);
+// Tunable launch-class edges (autotuner): edge0 in [kEdgeMin, kEdgeMax[0]],
+// edge0 < edge1 <= kEdgeMax[1]; (-1, -1) restores the defaults.  False for
+// values out of range (nothing changes).
+constexpr int kEdgeMin = 64;
+constexpr int kEdgeMax[2] = {288, 480};
+bool tridiag_set_edges(int e0, int e1);
+void tridiag_get_edges(int* e0, int* e1);
 int tridiag_smem_bytes(int cls, int n_max);
 int64_t tridiag_work_floats(int cls, int n, int n_max);
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
@@ -208,6 +215,13 @@ cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_byt
 cudaError_t launch_core_tridiag(int cls, const CoreDesc* d_desc, int n_items, int n_max,
                                 int* d_status, cudaStream_t s);
 std::string tridiag_selftest();
+// Failure-path test hook: per-device iteration caps of the solvers and the
+// limit of the tensor-core kernel's pipeline waits (negative: the default).
+cudaError_t tridiag_set_bisect_cap(int cap);
+cudaError_t refine64_set_bisect_cap(int cap);
+cudaError_t arrow_set_cap(int cap);
+cudaError_t jacobi_set_cap(int cap);
+cudaError_t tc_set_wait_ns(long long ns);
 // The mixed core marks an item for the FP64 re-solve when its estimated tail
 // lies below this fraction of the merged energy.
 constexpr double kRefineFrac = 2e-3;

@@ -45,6 +45,7 @@ namespace {
 constexpr int kArrowThreads = 128;
 constexpr int kArrowWarps = kArrowThreads / 32;
 constexpr int kArrowBisectMax = 64;
+__device__ int d_arrow_cap = kArrowBisectMax;  // lowered only by the failure-path test hook
 constexpr int kArrowModelIters = 16;
 constexpr int kArrowStage = 512;  // rows of the group's columns staged per pass
 constexpr int kArrowPerThread = kArrowStage / kArrowThreads;
@@ -304,7 +305,8 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
       bool done = !active || !((b - a) > atol);
       bool probed = false;
       int it = 0;
-      for (; it < kArrowBisectMax; ++it) {
+      const int cap = d_arrow_cap;
+      for (; it < cap; ++it) {
         if (__all_sync(0xffffffffu, done)) break;
         if (done) continue;
         float f = alpha - x, D = 0.f;
@@ -361,7 +363,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
         if (!have || !(y > a && y < b)) y = 0.5f * (a + b);
         x = y;
       }
-      if (active && !done) {
+      if (active && !done) {  // ran out of iterations (cap) without converging
         capped = 1;
         lam = 0.5f * (a + b);
       }
@@ -389,7 +391,8 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
       float a = glo, b = ghi;
       bool stuck = false;
       int it = 0;
-      for (; it < kArrowBisectMax; ++it) {
+      const int cap = d_arrow_cap;
+      for (; it < cap; ++it) {
         const float atol = fmaxf(afloor, 2.4e-7f * fmaxf(fabsf(a), fabsf(b)));
         const bool done = !active || stuck || !((b - a) > atol);
         if (__all_sync(0xffffffffu, done)) break;
@@ -409,7 +412,7 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
           b = nb;
         }
       }
-      if (active && it == kArrowBisectMax) capped = 1;
+      if (active && it == cap) capped = 1;
       if (active && sub == 0) s_lam[item][q] = 0.5f * (a + b);
     }
   }
@@ -446,6 +449,11 @@ __device__ __forceinline__ void arrow_group(const ArrowGroupView& V, int* __rest
 }
 
 }  // namespace
+
+cudaError_t arrow_set_cap(int cap) {
+  if (cap < 0) cap = kArrowBisectMax;
+  return cudaMemcpyToSymbol(d_arrow_cap, &cap, sizeof(int));
+}
 
 // A descriptor per candidate; group = {first descriptor, count}.
 __global__ void __launch_bounds__(kArrowThreads, 7)

@@ -18,6 +18,7 @@
 namespace csvd {
 
 constexpr int kJacobiMaxSweeps = 40;
+__device__ int d_jacobi_cap = kJacobiMaxSweeps;  // lowered only by the failure-path test hook
 constexpr int kBisectMaxIter = 64;
 
 // ------------------------------------------------------------- energy
@@ -44,6 +45,11 @@ energy_kernel(const EnergyDesc* __restrict__ descs) {
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     atomicAdd(d.out, t);
   }
+}
+
+cudaError_t jacobi_set_cap(int cap) {
+  if (cap < 0) cap = kJacobiMaxSweeps;
+  return cudaMemcpyToSymbol(d_jacobi_cap, &cap, sizeof(int));
 }
 
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
@@ -163,7 +169,8 @@ core_jacobi_kernel(const CoreDesc* __restrict__ descs, int* __restrict__ status)
 
   const float tol = 4.f * 5.9604645e-8f * sqrtf((float)(nr > 1 ? nr : 1));
   bool converged = (ncp < 2);
-  for (int sweep = 0; sweep < kJacobiMaxSweeps && !converged; ++sweep) {
+  const int cap = d_jacobi_cap;
+  for (int sweep = 0; sweep < cap && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int t = 0; t < ncp - 1; ++t) {

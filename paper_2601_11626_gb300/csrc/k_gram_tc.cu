@@ -33,7 +33,7 @@
 //   warp 1      one thread issues tcgen05.mma (M = 128, K = 16, N = the
 //               tile's valid columns rounded up to 16) into a fresh f32
 //               accumulator per stage (two in TMEM, alternating) and commits
-//   warps 10-13 add each stage's accumulator into the tile's running sum
+//   warps 10-17 add each stage's accumulator into the tile's running sum
 //               (round to nearest, kept in TMEM) and store the last one;
 //               the tensor cores' own accumulation truncates, so a long
 //               chain of additions inside one accumulator would shrink every
@@ -58,6 +58,9 @@ constexpr int kOpB = 3 * kTcPartBytes;  // hi, mid, lo of B
 constexpr int kOpBase = kTcStagesF * kTcStageF;  // operand ring after the staging ring
 constexpr int kAtomBytes = kTcBK * 128;          // one 64-column bf16 atom of 32 rows
 constexpr uint64_t kWaitNs = 2000000000ull;
+// limit of the pipeline waits (kWaitNs; shortened only by the failure-path
+// test hook); the drains after an abort always keep kWaitNs
+__device__ unsigned long long d_wait_ns = kWaitNs;
 // TMEM columns: two stage accumulators X and the running sum S of a tile
 constexpr uint32_t kXCol0 = 0, kSCol0 = 2 * kTcBN, kTmemCols = 512;
 static_assert(kTcConvWarps == 8, "four split warps per 64-column atom");
@@ -106,11 +109,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
                                           bool honour_abort = true) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = gtimer();
+  const uint64_t limit = honour_abort ? (uint64_t)d_wait_ns : kWaitNs;
   for (uint32_t it = 1; it < 0x7fffffffu; ++it) {
     if (mbar_try(a, parity)) return true;
     if ((it & 63u) == 0) {
       if (honour_abort && *abort_flag) return false;
-      if (gtimer() - t0 > kWaitNs) {
+      if (gtimer() - t0 > limit) {
         *abort_flag = 1;
         return false;
       }
@@ -191,6 +195,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.ld of 32 columns without the wait (pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
@@ -317,7 +339,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(x_full(a), 1);
-      mbar_init(x_empty(a), 4);
+      mbar_init(x_empty(a), kTcEpiWarps);
     }
     mbar_init(final_bar, 1);
     *abort_flag = 0;
@@ -504,8 +526,11 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     // ------------------------------------------------------ epilogue
     // Per stage: S = X (first stage) or S += X, kept in TMEM columns
     // [kSCol0, kSCol0 + 128); at the tile's last stage S + X goes to global
-    // memory instead.  Row r of the tile lives in TMEM lane r.
+    // memory instead.  Row r of the tile lives in TMEM lane r; two warps
+    // share each lane quarter, 64 columns each, and load a chunk of X and of
+    // S before waiting once.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int half = (warp - 2 - kTcConvWarps) >> 2;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int r = q * 32 + lane;
     uint32_t it = 0;
@@ -519,20 +544,23 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         if (!warp_wait(x_full(xb), (it >> 1) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const bool last = kb + 1 == nkb;
+        bool stored = false;
 #pragma unroll 1
-        for (int cc = 0; cc < kTcBN / 32; ++cc) {
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const int cc = 2 * half + c2;
           const int nv = ti.validB - cc * 32;  // valid columns of this chunk (same in every lane)
           if (nv <= 0) break;
+          uint32_t xv[32], sv[32];
+          tmem_ld32_async(tmem_base + lane_off + kXCol0 + xb * (uint32_t)kTcBN + cc * 32, xv);
+          if (kb > 0) tmem_ld32_async(tmem_base + lane_off + kSCol0 + cc * 32, sv);
+          tmem_wait_ld();
           float v[32];
-          tmem_ld32(tmem_base + lane_off + kXCol0 + xb * (uint32_t)kTcBN + cc * 32, v);
-          if (kb > 0) {
-            float sacc[32];
-            tmem_ld32(tmem_base + lane_off + kSCol0 + cc * 32, sacc);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] += sacc[e];
-          }
+          for (int e = 0; e < 32; ++e)
+            v[e] = __uint_as_float(xv[e]) + (kb > 0 ? __uint_as_float(sv[e]) : 0.f);
           if (!last) {
             tmem_st32(tmem_base + lane_off + kSCol0 + cc * 32, v);
+            stored = true;
           } else if (r < ti.validA) {
             float* o = ti.out + (int64_t)r * ti.ldo + cc * 32;
             if (vec) {
@@ -554,7 +582,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
             }
           }
         }
-        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        if (stored) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(x_empty(xb));
@@ -585,6 +613,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   });
   return fn;
+}
+
+cudaError_t tc_set_wait_ns(long long ns) {
+  const unsigned long long v = ns < 0 ? kWaitNs : (unsigned long long)ns;
+  return cudaMemcpyToSymbol(d_wait_ns, &v, sizeof(v));
 }
 
 bool tc_tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out) {

@@ -24,6 +24,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBisect64 = 128;
+__device__ int d_bisect64_cap = kBisect64;  // lowered only by the failure-path test hook
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -181,14 +182,15 @@ core_refine64_kernel(const CoreDesc* __restrict__ d0, int n0, const CoreDesc* __
     for (int q = tid; q < d.r_new; q += kThreads) {
       double a = glo, b = ghi;
       int it = 0;
-      for (; it < kBisect64; ++it) {
+      const int cap = d_bisect64_cap;
+      for (; it < cap; ++it) {
         if (!(b - a > fmax(atol, 4e-16 * fmax(fabs(a), fabs(b))))) break;
         const double x = 0.5 * (a + b);
         if (!(x > a && x < b)) break;
         if (sturm64(dv, v, n, x, pivmin) > n - 1 - q) b = x;
         else a = x;
       }
-      if (it == kBisect64) capped = 1;
+      if (it == cap) capped = 1;
       const double lam = 0.5 * (a + b);
       p[q] = lam;
       top += lam;
@@ -217,6 +219,11 @@ core_refine64_kernel(const CoreDesc* __restrict__ d0, int n0, const CoreDesc* __
 }
 
 }  // namespace
+
+cudaError_t refine64_set_bisect_cap(int cap) {
+  if (cap < 0) cap = kBisect64;
+  return cudaMemcpyToSymbol(d_bisect64_cap, &cap, sizeof(int));
+}
 
 size_t refine64_smem_bytes(int n_max) { return sizeof(double) * (4 * (size_t)n_max + 16); }
 

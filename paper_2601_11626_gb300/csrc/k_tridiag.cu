@@ -40,6 +40,7 @@
 //  4. FP64 epilogue: sigma~, tail = discarded_state + tr(T) - sum top, the
 //     subtraction form sum ||A||^2 - sum sigma~^2, and the accept flag; the
 //     block energy ||A||^2 is the trace of A^T A unless given.
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -50,6 +51,8 @@ namespace csvd {
 namespace {
 
 constexpr int kBisectMax = 64;
+// iteration cap of the bisection (kBisectMax; lowered only by the failure-path test hook)
+__device__ int d_bisect_cap = kBisectMax;
 constexpr int kTile = 32;
 constexpr int kTileFloats = kTile * kTile;
 constexpr int kVecs = 9;  // dv, ev, v (2), p (2), w, column (2)
@@ -697,7 +700,8 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
     const unsigned shift = (unsigned)((lane / g) * g);
     const unsigned gmask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << shift);
     int it = 0;
-    for (; it < kBisectMax; ++it) {
+    const int cap = d_bisect_cap;
+    for (; it < cap; ++it) {
       // every lane of the warp runs the same number of iterations
       const bool done = !active || stuck || !((b - a) > fmaxf(atol, 2.4e-7f * fmaxf(fabsf(a), fabsf(b))));
       if (__all_sync(0xffffffffu, done)) break;
@@ -716,7 +720,7 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
         b = nb;
       }
     }
-    if (active && it == kBisectMax) capped = 1;
+    if (active && it == cap) capped = 1;
     if (active && sub == 0) lam[q] = 0.5f * (a + b);
   }
   if (capped) atomicOr(status, kStatusBisectCap);
@@ -747,9 +751,36 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
 
 }  // namespace
 
+cudaError_t tridiag_set_bisect_cap(int cap) {
+  if (cap < 0) cap = kBisectMax;
+  return cudaMemcpyToSymbol(d_bisect_cap, &cap, sizeof(int));
+}
+
+// Launch-class edges: cores of size n <= edge0 take class 0, n <= edge1
+// class 1, larger ones class 2 (defaults kClass[0..1].max_n; set by the
+// autotuner within [kEdgeMin, kEdgeMax[c]]).
+static std::atomic<int> g_edge0{kClass[0].max_n}, g_edge1{kClass[1].max_n};
+
+bool tridiag_set_edges(int e0, int e1) {
+  if (e0 < 0 && e1 < 0) {
+    g_edge0 = kClass[0].max_n;
+    g_edge1 = kClass[1].max_n;
+    return true;
+  }
+  if (e0 < kEdgeMin || e0 > kEdgeMax[0] || e1 <= e0 || e1 > kEdgeMax[1]) return false;
+  g_edge0 = e0;
+  g_edge1 = e1;
+  return true;
+}
+
+void tridiag_get_edges(int* e0, int* e1) {
+  *e0 = g_edge0;
+  *e1 = g_edge1;
+}
+
 int tridiag_class(int n) {
-  for (int c = 0; c < 2; ++c)
-    if (n <= kClass[c].max_n) return c;
+  if (n <= g_edge0) return 0;
+  if (n <= g_edge1) return 1;
   return 2;
 }
 
@@ -792,12 +823,19 @@ static cudaError_t launch_class(const CoreDesc* d_desc, int n_items, int smem_by
 // string or the first failure.
 std::string tridiag_selftest() {
   char buf[256];
+  int e0, e1;
+  tridiag_get_edges(&e0, &e1);
   for (int n = 1; n <= 1024; ++n) {
     const int cls = tridiag_class(n);
-    if ((n <= 192) != (cls == 0) || (n > 192 && n <= 320) != (cls == 1))
+    if ((n <= e0) != (cls == 0) || (n > e0 && n <= e1) != (cls == 1))
       return "launch class of n = " + std::to_string(n);
-    const int class_max = cls == 0 ? 192 : cls == 1 ? 320 : 1024;
-    for (int n_max = n; n_max <= class_max; ++n_max) {
+  }
+  // every core size a class can receive under any tunable edges
+  for (int n = 1; n <= 1024; ++n) for (int cls = 0; cls < 3; ++cls) {
+    const int class_max = cls == 0 ? kEdgeMax[0] : cls == 1 ? kEdgeMax[1] : 1024;
+    const int class_min = cls == 0 ? 1 : kEdgeMin + 1;
+    if (n < class_min || n > class_max) continue;
+    for (int n_max = n; n_max <= class_max; n_max += (cls == 2 ? 3 : 1)) {
       const int smem = tridiag_smem_bytes(cls, n_max);
       if (smem <= 0 || smem > 227 * 1024) {
         snprintf(buf, sizeof buf, "shared memory %d B for class %d, n_max %d", smem, cls, n_max);

@@ -37,7 +37,8 @@ struct TcTile {
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcBox = 32;
 constexpr int kTcStagesF = 3, kTcStagesB = 2;
 constexpr int kTcConvWarps = 8;  // warps splitting f32 into bf16 parts
-constexpr int kTcThreads = (2 + kTcConvWarps + 4) * 32;
+constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter
+constexpr int kTcThreads = (2 + kTcConvWarps + kTcEpiWarps) * 32;
 constexpr int kTcBoxBytes = kTcBK * kTcBox * 4;                 // 4 KB
 constexpr int kTcStageF = 2 * (kTcBM / kTcBox) * kTcBoxBytes;   // 32 KB: A and B, f32
 constexpr int kTcPartBytes = kTcBK * kTcBM * 2;                 // 8 KB: one bf16 part

@@ -86,6 +86,9 @@ def _sig(lib):
     lib.csvd_tail_grad.argtypes = [VP, I64, I64, I32, P(Block), P(Block), I32, D, VP]
     lib.csvd_block_energy.argtypes = [P(Block), I32, I64, VP, P(D)]
     lib.csvd_set_allocator.argtypes = [VP, VP, VP]
+    lib.csvd_debug_limits.argtypes = [I32, I32, I64]
+    lib.csvd_tune_set.argtypes = [I32, I32]
+    lib.csvd_tune_get.argtypes = [P(I32), P(I32)]
     lib.csvd_score_one_noalloc.argtypes = [VP, P(Block), D, VP, VP, VP, VP]
     lib.csvd_score_one_noalloc.restype = C.c_int
     lib.csvd_launch_count.restype = C.c_int64
@@ -98,7 +101,8 @@ def _sig(lib):
                  "csvd_tail_error", "csvd_incr_free", "csvd_score", "csvd_score_columns", "csvd_bounds",
                  "csvd_stream_init", "csvd_stream_push", "csvd_stream_count",
                  "csvd_stream_cluster", "csvd_stream_free",
-                 "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator"):
+                 "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator",
+                 "csvd_debug_limits", "csvd_tune_set", "csvd_tune_get"):
         getattr(lib, name).restype = C.c_int
 
 
@@ -555,6 +559,12 @@ class TailEnergy(torch.autograd.Function):
 
 def tail_energy(blocks, r, working_rank=None):
     return TailEnergy.apply(r, working_rank, *blocks)
+
+
+def debug_limits(jacobi_sweeps: int = -1, solver_iters: int = -1, wait_ns: int = -1):
+    """Failure-path test hook (csvd_debug_limits): solver caps and the
+    tensor-core pipeline wait limit of the current device; -1 restores."""
+    _check(lib().csvd_debug_limits(jacobi_sweeps, solver_iters, wait_ns))
 
 
 def launch_count() -> int:

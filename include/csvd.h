@@ -241,6 +241,27 @@ csvd_status csvd_tail_grad(const float* U, int64_t ldu, int64_t m, int32_t r,
                            const csvd_block* blocks, const csvd_block* grads, int32_t n,
                            double g, void* cuda_stream);
 
+/* Eckart-Young tail energy of a basis (Thm. 4; the differentiable
+ * objective of the spec extension): resid_sq[j] = ||(I - U U^T) A_j||_F^2
+ * for every block (host array of n doubles), U m x r orthonormal (row-major,
+ * device, ldu).  P_j = U^T A_j is formed by a GEMM; the residual is not
+ * stored: its squares are summed tile by tile (exact squares, compensated
+ * FP32 sums, FP64 totals).  f32 blocks.  Syncs. */
+csvd_status csvd_tail_energy(const float* U, int64_t ldu, int64_t m, int32_t r,
+                             const csvd_block* blocks, int32_t n, void* cuda_stream,
+                             double* resid_sq);
+
+/* Top-r left singular basis of the concatenation of n blocks: the
+ * incremental estimator (Lemma 1, Cor. 3) at rank working_rank (>= r), then
+ * `refine` sweeps of subspace iteration Y = M M^T U, each followed by taking
+ * the left singular vectors of Y (a rank-r append) -- each sweep shrinks the
+ * angle to the exact top-r subspace by (sigma_{r+1} / sigma_r)^2.  Writes
+ * U_out (m x r_eff, row-major, device, ldu >= r), r_eff = min(r, rank).
+ * Allocates its temporary states with cudaMalloc.  Syncs. */
+csvd_status csvd_top_basis(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
+                           int32_t working_rank, int32_t refine, void* cuda_stream, float* U_out,
+                           int64_t ldu, int32_t* r_eff);
+
 /* Y = sum_j A_j (A_j^T U) = M M^T U for the concatenation M of the blocks:
  * one sweep of subspace iteration, used to refine a basis U (m x r,
  * row-major, device, ldu) towards the top-r left singular subspace of M

@@ -2202,6 +2202,114 @@ extern "C" csvd_status csvd_reconstruct(const float* U, int64_t ldu, const float
   return CSVD_OK;
 }
 
+// Eckart-Young tail energy of a basis: per block ||(I - U U^T) A_j||_F^2,
+// P = U^T A_j by the batched GEMM, then the residual's squares summed tile
+// by tile without storing it.
+extern "C" csvd_status csvd_tail_energy(const float* U, int64_t ldu, int64_t m, int32_t r,
+                                        const csvd_block* blocks, int32_t n, void* cuda_stream,
+                                        double* resid_sq) {
+  if (!U || !blocks || !resid_sq || n < 0 || m < 1 || r < 1 || ldu < r)
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "f32 blocks only");
+  }
+  if (n == 0) return CSVD_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  Layout L;
+  const size_t o_out = L.add(sizeof(double) * (size_t)n);
+  std::vector<size_t> oP(n);
+  for (int i = 0; i < n; ++i) oP[i] = L.add(sizeof(float) * (size_t)r * blocks[i].k);
+  GemmBatch gP;
+  std::vector<ResidDesc> rd;
+  int max_k = 1;
+  auto fill = [&](char* base) {
+    gP = GemmBatch();
+    rd.clear();
+    for (int i = 0; i < n; ++i) {
+      const int k = (int)blocks[i].k;
+      max_k = std::max(max_k, k);
+      float* P = reinterpret_cast<float*>(base + oP[i]);
+      gP.add(gemm(U, ldu, 1, blocks[i].ptr, blocks[i].ld, 0, P, k, 0, r, k, (int)m));
+      rd.push_back(ResidDesc{reinterpret_cast<const float*>(blocks[i].ptr), blocks[i].ld, U, ldu, P,
+                             k, (int)m, k, reinterpret_cast<double*>(base + o_out) + i});
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  gP.pack(probe);
+  probe.add(rd);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  gP.pack(pk);
+  const size_t o_rd = pk.add(rd);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  CUDA_TRY(cudaMemsetAsync(w.base + o_out, 0, sizeof(double) * (size_t)n, s));
+  CUDA_TRY(gP.launch(dbase, s));
+  CUDA_TRY(launch_resid_energy(reinterpret_cast<ResidDesc*>(dbase + o_rd), n, (int)m, max_k, r, s));
+  CUDA_TRY(cudaMemcpyAsync(resid_sq, w.base + o_out, sizeof(double) * (size_t)n,
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CSVD_OK;
+}
+
+// Top-r left basis of a block collection: the incremental estimator at a
+// working rank, then `refine` sweeps of subspace iteration (Y = M M^T U,
+// orthonormalised as the left singular vectors of Y by a rank-r append).
+extern "C" csvd_status csvd_top_basis(const csvd_block* blocks, int32_t n, int64_t m, int32_t r,
+                                      int32_t working_rank, int32_t refine, void* cuda_stream,
+                                      float* U_out, int64_t ldu, int32_t* r_eff) {
+  if (!blocks || n < 1 || m < 1 || r < 1 || !U_out || ldu < r || refine < 0)
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  if (working_rank < r) working_rank = r;
+  working_rank = (int32_t)std::min<int64_t>(working_rank, m);
+  if (r > working_rank) return fail(CSVD_ERR_ARG, "r > min(m, working rank)");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  csvd_state st = nullptr;
+  CSVD_TRY(csvd_incr_init(&st, m, working_rank, CSVD_PLAIN_FP32, cuda_stream));
+  csvd_status rc = CSVD_OK;
+  for (int i = 0; i < n && rc == CSVD_OK; ++i) rc = csvd_incr_append(st, &blocks[i]);
+  int32_t rk = 0;
+  if (rc == CSVD_OK) rc = csvd_incr_sigma(st, nullptr, &rk);
+  const int rr = std::min<int>(r, rk);
+  if (r_eff) *r_eff = rr;
+  if (rc == CSVD_OK && rr > 0)
+    rc = cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, st->U[st->cur], sizeof(float) * st->r,
+                           sizeof(float) * rr, m, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+             ? CSVD_OK
+             : fail(CSVD_ERR_CUDA, "basis copy failed");
+  csvd_incr_free(st);
+  if (rc != CSVD_OK || rr == 0) return rc;
+  // subspace iteration: Y = M M^T U, U <- left singular vectors of Y
+  float* Y = static_cast<float*>(dev_alloc(sizeof(float) * (size_t)m * rr, s));
+  if (!Y) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  for (int it = 0; it < refine && rc == CSVD_OK; ++it) {
+    rc = csvd_gram_apply(U_out, ldu, m, rr, blocks, n, Y, rr, cuda_stream);
+    csvd_state q = nullptr;
+    if (rc == CSVD_OK) rc = csvd_incr_init(&q, m, rr, CSVD_PLAIN_FP32, cuda_stream);
+    if (rc == CSVD_OK) {
+      const csvd_block yb{Y, rr, rr, CSVD_F32, 0};
+      rc = csvd_incr_append(q, &yb);
+      int32_t qk = 0;
+      if (rc == CSVD_OK) rc = csvd_incr_sigma(q, nullptr, &qk);
+      if (rc == CSVD_OK && qk == rr)
+        rc = cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, q->U[q->cur], sizeof(float) * q->r,
+                               sizeof(float) * rr, m, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+                 ? CSVD_OK
+                 : fail(CSVD_ERR_CUDA, "basis copy failed");
+    }
+    if (q) csvd_incr_free(q);
+  }
+  dev_free(Y, s);
+  return rc;
+}
+
 extern "C" csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m,
                                          void* cuda_stream, double* energy_host) {
   if (!blocks || n < 0 || m < 1 || !energy_host) return fail(CSVD_ERR_ARG, "bad arguments");

@@ -137,6 +137,19 @@ struct EnergyDesc {
   double* out;
 };
 
+// Residual energy of one block: out += ||A - U P||_F^2 (A m x k f32, lda;
+// U m x r, ldu; P r x k, ldp).
+struct ResidDesc {
+  const float* A;
+  int64_t lda;
+  const float* U;
+  int64_t ldu;
+  const float* P;
+  int64_t ldp;
+  int m, k;
+  double* out;
+};
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -190,6 +203,8 @@ cudaError_t launch_apply_q(const ApplyQDesc* d_desc, int n_items, int max_cols,
                            cudaStream_t s);
 cudaError_t launch_energy(const EnergyDesc* d_desc, int n_items, int max_chunks,
                           cudaStream_t s);
+cudaError_t launch_resid_energy(const ResidDesc* d_desc, int n_items, int max_m, int max_k, int r,
+                                cudaStream_t s);
 // Column energies: out[c] += sum_i A_ic^2 for every column of every item
 // (EnergyDesc.out points at k doubles, zeroed before the launch).
 cudaError_t launch_col_energy(const EnergyDesc* d_desc, int n_items, int max_k, int max_m,

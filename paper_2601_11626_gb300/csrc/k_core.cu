@@ -100,6 +100,79 @@ cudaError_t launch_col_energy(const EnergyDesc* d_desc, int n_items, int max_k, 
   return cudaGetLastError();
 }
 
+// Residual energies without materialising the residual: for every block
+// sum_ij (A - U P)_ij^2 with P = U^T A given (r x k, ld k).  A CTA of 256
+// threads takes a 64 x 64 tile of one block (each thread a 4 x 4 patch),
+// accumulates U P over r in chunks of 32 staged in shared memory, and sums
+// the squares of A - U P exactly (FMA error of the square, two-sum), one
+// FP64 atomic per thread group.
+__global__ void __launch_bounds__(256)
+resid_energy_kernel(const ResidDesc* __restrict__ descs, int r) {
+  const ResidDesc d = descs[blockIdx.z];
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  if (row0 >= d.m || col0 >= d.k) return;
+  __shared__ float su[64][33];  // U rows x r chunk
+  __shared__ float sp[32][64];  // r chunk x P columns
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;  // 16 x 16 threads, 4 x 4 each
+  float acc[4][4] = {};
+  for (int c0 = 0; c0 < r; c0 += 32) {
+    for (int e = tid; e < 64 * 32; e += 256) {
+      const int i = e >> 5, j = e & 31;
+      const int gi = row0 + i, gj = c0 + j;
+      su[i][j] = (gi < d.m && gj < r) ? d.U[(int64_t)gi * d.ldu + gj] : 0.f;
+    }
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int i = e >> 6, j = e & 63;
+      const int gi = c0 + i, gj = col0 + j;
+      sp[i][j] = (gi < r && gj < d.k) ? d.P[(int64_t)gi * d.ldp + gj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < 32; ++l) {
+      float ua[4], pb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ua[a] = su[tr * 4 + a][l];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) pb[b] = sp[l][tc * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ua[a], pb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  float s = 0.f, comp = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gi = row0 + tr * 4 + a;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gj = col0 + tc * 4 + b;
+      if (gi < d.m && gj < d.k) {
+        const float x = d.A[(int64_t)gi * d.lda + gj] - acc[a][b];
+        const float p = x * x;
+        const float e = fmaf(x, x, -p);
+        const float t = s + p;
+        const float z = t - s;
+        comp += ((s - (t - z)) + (p - z)) + e;
+        s = t;
+      }
+    }
+  }
+  double v = warp_sum_d((double)s + (double)comp);
+  if ((tid & 31) == 0) atomicAdd(d.out, v);
+}
+
+cudaError_t launch_resid_energy(const ResidDesc* d_desc, int n_items, int max_m, int max_k, int r,
+                                cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((max_k + 63) / 64, (max_m + 63) / 64, n_items);
+  prof_begin(s);
+  resid_energy_kernel<<<grid, 256, 0, s>>>(d_desc, r);
+  prof_end("resid_energy", s);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ shared epilogue
 // vals[0..nv) non-increasing; writes sigma~, tails and the accept flag.
 // Called by warp 0 only; vals_are_sq says whether vals hold sigma^2.

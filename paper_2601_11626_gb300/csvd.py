@@ -88,6 +88,8 @@ def _sig(lib):
     lib.csvd_set_allocator.argtypes = [VP, VP, VP]
     lib.csvd_debug_limits.argtypes = [I32, I32, I64]
     lib.csvd_tune_set.argtypes = [I32, I32]
+    lib.csvd_tail_energy.argtypes = [VP, I64, I64, I32, P(Block), I32, VP, P(D)]
+    lib.csvd_top_basis.argtypes = [P(Block), I32, I64, I32, I32, I32, VP, VP, I64, P(I32)]
     lib.csvd_tune_get.argtypes = [P(I32), P(I32)]
     lib.csvd_score_one_noalloc.argtypes = [VP, P(Block), D, VP, VP, VP, VP]
     lib.csvd_score_one_noalloc.restype = C.c_int
@@ -102,7 +104,8 @@ def _sig(lib):
                  "csvd_stream_init", "csvd_stream_push", "csvd_stream_count",
                  "csvd_stream_cluster", "csvd_stream_free",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator",
-                 "csvd_debug_limits", "csvd_tune_set", "csvd_tune_get"):
+                 "csvd_debug_limits", "csvd_tune_set", "csvd_tune_get", "csvd_tail_energy",
+                 "csvd_top_basis"):
         getattr(lib, name).restype = C.c_int
 
 
@@ -515,23 +518,26 @@ def gram_apply(U: torch.Tensor, blocks) -> torch.Tensor:
     return Y
 
 
-def _basis(blocks, r, working_rank, refine=2):
-    """Top-r basis: the incremental estimator at working rank, then
-    ``refine`` sweeps of subspace iteration (orthonormalised through an
-    incremental append of M M^T U)."""
+def top_basis(blocks, r, working_rank=None, refine=2):
+    """Top-r left basis of the concatenation (csvd_top_basis): incremental
+    estimator at ``working_rank``, then ``refine`` subspace-iteration sweeps."""
     m = blocks[0].shape[0]
-    st = IncrSVD(m, working_rank or r)
-    for b in blocks:
-        st.append(b)
-    U = st.basis()[:, :r].contiguous()
-    st.close()
-    for _ in range(refine):
-        Y = gram_apply(U, list(blocks))
-        q = IncrSVD(m, r)
-        q.append(Y)
-        U = q.basis().contiguous()
-        q.close()
-    return U
+    U = torch.empty(m, r, device="cuda", dtype=torch.float32)
+    reff = C.c_int32()
+    _check(lib().csvd_top_basis(_blocks(blocks, m), len(blocks), m, r, int(working_rank or r),
+                                int(refine), _stream(), C.c_void_p(U.data_ptr()), U.stride(0),
+                                C.byref(reff)))
+    return U[:, :reff.value]
+
+
+def residual_energy(U: torch.Tensor, blocks) -> np.ndarray:
+    """||(I - U U^T) A_j||_F^2 of every block (csvd_tail_energy), FP64."""
+    m, r = U.shape
+    U = U.contiguous()
+    out = (C.c_double * max(len(blocks), 1))()
+    _check(lib().csvd_tail_energy(C.c_void_p(U.data_ptr()), U.stride(0), m, r, _blocks(blocks, m),
+                                  len(blocks), _stream(), out))
+    return np.frombuffer(out, dtype=np.float64, count=len(blocks)).copy()
 
 
 class TailEnergy(torch.autograd.Function):
@@ -542,9 +548,8 @@ class TailEnergy(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, r, working_rank, *blocks):
-        U = _basis(blocks, r, working_rank)
-        res = tail_grad(U, list(blocks), 0.5)
-        e = block_energy(res).sum()
+        U = top_basis(list(blocks), r, working_rank)
+        e = float(residual_energy(U, list(blocks)).sum())
         ctx.r, ctx.working_rank = r, working_rank
         ctx.save_for_backward(*blocks)
         return torch.tensor(e, dtype=torch.float64, device=blocks[0].device)
@@ -552,7 +557,7 @@ class TailEnergy(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gE):
         blocks = ctx.saved_tensors
-        U = _basis(blocks, ctx.r, ctx.working_rank)
+        U = top_basis(list(blocks), ctx.r, ctx.working_rank)
         grads = tail_grad(U, list(blocks), float(gE))
         return (None, None, *grads)
 

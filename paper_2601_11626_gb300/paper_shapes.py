@@ -70,7 +70,7 @@ def run(name, algo="approx", sort_mode="frobenius", scale=1.0, precision="mixed"
         worst, num, den = 0.0, 0.0, 0.0
         for members in groups.values():
             sub = [blocks[i] for i in members]
-            U = csvd._basis(sub, p["r"], p["r"] + 16, refine=2)
+            U = csvd.top_basis(sub, p["r"], p["r"] + 16, refine=2)
             d = csvd.reconstruct(U, [1.0] * U.shape[1], sub, want_v=False)
             worst = max(worst, d.rel_error)
             num += float(d.resid_sq.sum())

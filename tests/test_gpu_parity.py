@@ -624,3 +624,27 @@ def test_argument_errors_return_status(csvd):
     assert csvd.lib().csvd_incr_append(st.handle, ctypes.byref(b)) == csvd.Status.ERR_ARG
     st.append(x)   # still usable after rejected calls
     assert st.rank == 4
+
+
+def test_residual_energy_and_top_basis_against_oracle(csvd):
+    """csvd_tail_energy: ||(I - U U^T) A_j||^2 for a given orthonormal basis
+    against the FP64 value, per block; csvd_top_basis: the refined basis
+    spans the oracle's top-r subspace of the gapped collection (its tail
+    energy equals the Eckart-Young tail)."""
+    w = synth.grad_c5(n_blocks=8, m=512, k=64)
+    blocks = w["fd"]
+    r = 128
+    u, _ = oexact.top_left_basis(blocks, r)
+    U = torch.tensor(u, dtype=torch.float32, device="cuda")
+    got = csvd.residual_energy(U, [b.cuda() for b in blocks])
+    u32 = U.double().cpu().numpy()
+    for j, b in enumerate(blocks):
+        a = b.double().numpy()
+        res = a - u32 @ (u32.T @ a)
+        want = float(np.sum(res * res))
+        _check_tail(got[j], want, float(np.sum(a * a)))
+    Ug = csvd.top_basis([b.cuda() for b in blocks], r, r + 32, refine=2)
+    assert Ug.shape == (512, r)
+    tail = float(csvd.residual_energy(Ug, [b.cuda() for b in blocks]).sum())
+    energy = sum(float((b.double() ** 2).sum()) for b in blocks)
+    _check_tail(tail, oexact.tail_sq(blocks, r), energy)

@@ -251,6 +251,19 @@ csvd_status csvd_tail_energy(const float* U, int64_t ldu, int64_t m, int32_t r,
                              const csvd_block* blocks, int32_t n, void* cuda_stream,
                              double* resid_sq);
 
+/* Randomized range-finder tail estimate (the discussion section's sketching
+ * variant of the estimator): Y = sum_i A_i Omega_i with the caller's test
+ * matrices Omega_i (k_i x l, row-major, device, ld l; l = r + oversampling,
+ * r <= l <= m), power_iters iterations Y <- M M^T Q (Q the left singular
+ * basis of Y), U_r = the top-r left singular vectors of Y, and
+ * *tail_sq = sum_i ||(I - U_r U_r^T) A_i||_F^2 -- the explicit residual of
+ * a rank-r projection, hence never below the optimal E_r^2 (Thm. 4) for any
+ * draw: a certified estimate.  U_out (m x r, device, ldu; may be NULL)
+ * receives U_r.  f32 blocks.  Syncs. */
+csvd_status csvd_randomized_tail(const csvd_block* blocks, const float* const* omegas, int32_t n,
+                                 int64_t m, int32_t r, int32_t l, int32_t power_iters,
+                                 void* cuda_stream, double* tail_sq, float* U_out, int64_t ldu);
+
 /* Top-r left singular basis of the concatenation of n blocks: the
  * incremental estimator (Lemma 1, Cor. 3) at rank working_rank (>= r), then
  * `refine` sweeps of subspace iteration Y = M M^T U, each followed by taking

@@ -1438,11 +1438,18 @@ static csvd_status block_energies(const csvd_block* blocks, const std::vector<in
 struct SpanState {
   int64_t m = 0;
   int rho = 0;
-  float* Qf = nullptr;        // m x m capacity, ld = m
+  float* Qf = nullptr;        // m x m capacity, ld = m (from the installed allocator)
+  cudaStream_t s = nullptr;   // stream of Qf's allocation
   double energy = 0.0;
   double proj = 0.0;          // sum_i ||Q_{i-1}^T A_i||^2 over the accepted blocks
   std::vector<double> mu;     // residual singular values (multiset)
-  ~SpanState() { cudaFree(Qf); }
+  bool alloc(int64_t m_, cudaStream_t st) {
+    m = m_;
+    s = st;
+    Qf = static_cast<float*>(dev_alloc(sizeof(float) * (size_t)m * m, s));
+    return Qf != nullptr;
+  }
+  ~SpanState() { dev_free(Qf, s); }
 };
 
 // R_j = (I - Qf Qf^T) A_j (one re-orthogonalisation pass) for several blocks,
@@ -1561,8 +1568,11 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
     CSVD_TRY(check_block(&blocks[i], m));
     if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "bounds take f32 blocks");
   }
-  int* d_status = nullptr;
-  CUDA_TRY(cudaMalloc(&d_status, sizeof(int)));
+  Workspace ws_status;
+  ws_status.s = s;
+  ws_status.base = static_cast<char*>(dev_alloc(sizeof(int), s));
+  if (!ws_status.base) return fail(CSVD_ERR_OOM, "status allocation failed");
+  int* d_status = ws_status.at<int>(0);
   CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
   std::vector<int> all(n);
   std::iota(all.begin(), all.end(), 0);
@@ -1584,9 +1594,7 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
   }
   if (st == CSVD_OK && residual_sq) {
     SpanState sp;
-    sp.m = m;
-    cudaError_t e = cudaMalloc(&sp.Qf, sizeof(float) * m * m);
-    if (e != cudaSuccess) st = fail(CSVD_ERR_OOM, "span basis allocation failed");
+    if (!sp.alloc(m, s)) st = fail(CSVD_ERR_OOM, "span basis allocation failed");
     double Ssofar = 0.0;
     for (int i = 0; i < n && st == CSVD_OK; ++i) {
       Workspace w;
@@ -1614,7 +1622,6 @@ extern "C" csvd_status csvd_bounds(const csvd_block* blocks, int32_t n, int64_t 
     csvd_incr_free(inc);
   }
   cudaStreamSynchronize(s);
-  cudaFree(d_status);
   return st;
 }
 
@@ -1869,8 +1876,7 @@ csvd_status cluster_residual(Driver& D, int sort_mode, std::vector<std::vector<i
     const int anchor = remaining.front();
     remaining.erase(remaining.begin());
     SpanState sp;
-    sp.m = D.m;
-    CUDA_TRY(cudaMalloc(&sp.Qf, sizeof(float) * D.m * D.m));
+    if (!sp.alloc(D.m, D.s)) return fail(CSVD_ERR_OOM, "span basis allocation failed");
     std::vector<int> members{anchor};
     {
       std::vector<double> e1, t1;
@@ -2040,7 +2046,11 @@ extern "C" csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t
   D.eps = eps;
   D.precision = precision;
   D.s = static_cast<cudaStream_t>(cuda_stream);
-  CUDA_TRY(cudaMalloc(&D.d_status, sizeof(int)));
+  Workspace ws_status;
+  ws_status.s = D.s;
+  ws_status.base = static_cast<char*>(dev_alloc(sizeof(int), D.s));
+  if (!ws_status.base) return fail(CSVD_ERR_OOM, "status allocation failed");
+  D.d_status = ws_status.at<int>(0);
   CUDA_TRY(cudaMemsetAsync(D.d_status, 0, sizeof(int), D.s));
   std::vector<int> all(n);
   std::iota(all.begin(), all.end(), 0);
@@ -2057,7 +2067,6 @@ extern "C" csvd_status csvd_cluster(const csvd_block* blocks, int32_t n, int64_t
     else rc = cluster_weyl(D, clusters, est);
   }
   cudaStreamSynchronize(D.s);
-  cudaFree(D.d_status);
   if (rc != CSVD_OK) return rc;
   int64_t raw = 0, stored = 0;
   for (size_t c = 0; c < clusters.size(); ++c) {
@@ -2308,6 +2317,78 @@ extern "C" csvd_status csvd_top_basis(const csvd_block* blocks, int32_t n, int64
   }
   dev_free(Y, s);
   return rc;
+}
+
+// Randomized range-finder tail estimate: Y = sum_i A_i Omega_i, q power
+// iterations Y <- M M^T Q (Q the left singular basis of Y), U_r the top-r
+// left singular vectors of Y, and the explicit residual energy of U_r.
+extern "C" csvd_status csvd_randomized_tail(const csvd_block* blocks, const float* const* omegas,
+                                            int32_t n, int64_t m, int32_t r, int32_t l,
+                                            int32_t power_iters, void* cuda_stream,
+                                            double* tail_sq, float* U_out, int64_t ldu) {
+  if (!blocks || !omegas || !tail_sq || n < 1 || m < 1 || r < 1 || l < r || l > m ||
+      power_iters < 0 || (U_out && ldu < r))
+    return fail(CSVD_ERR_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    CSVD_TRY(check_block(&blocks[i], m));
+    if (blocks[i].dtype != CSVD_F32) return fail(CSVD_ERR_UNIMPLEMENTED, "f32 blocks only");
+    if (!omegas[i]) return fail(CSVD_ERR_ARG, "NULL test matrix");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // 1. Y = sum_i A_i Omega_i (one GEMM per block, accumulating)
+  Layout L;
+  const size_t oY = L.add(sizeof(float) * (size_t)m * l);
+  const size_t oQ = L.add(sizeof(float) * (size_t)m * l);
+  const size_t oU = L.add(sizeof(float) * (size_t)m * r);
+  std::vector<GemmBatch> gY(n);
+  auto fill = [&](char* base) {
+    float* Y = reinterpret_cast<float*>(base + oY);
+    for (int i = 0; i < n; ++i) {
+      gY[i] = GemmBatch();
+      gY[i].add(gemm(blocks[i].ptr, blocks[i].ld, 0, omegas[i], l, 0, Y, l, 0, (int)m, l,
+                     (int)blocks[i].k, 1.f, i == 0 ? nullptr : Y, l, 0, i == 0 ? 0.f : 1.f));
+    }
+  };
+  fill(reinterpret_cast<char*>(uintptr_t(1) << 20));
+  Pack probe;
+  for (auto& g : gY) g.pack(probe);
+  const size_t o_desc = L.add(probe.buf.size());
+  Workspace w;
+  w.s = s;
+  w.base = static_cast<char*>(dev_alloc(L.size, s));
+  if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
+  fill(w.base);
+  Pack pk;
+  for (auto& g : gY) g.pack(pk);
+  char* dbase = w.base + o_desc;
+  CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  for (auto& g : gY) CUDA_TRY(g.launch(dbase, s));
+  float* Y = w.at<float>(oY);
+  float* Q = w.at<float>(oQ);
+  float* U = w.at<float>(oU);
+  const csvd_block yb{Y, l, l, CSVD_F32, 0};
+  int32_t rk = 0;
+  // 2. power iterations: Q = left singular basis of Y, Y = M M^T Q
+  for (int it = 0; it < power_iters; ++it) {
+    CSVD_TRY(csvd_top_basis(&yb, 1, m, l, l, 0, cuda_stream, Q, l, &rk));
+    if (rk < l) CUDA_TRY(cudaMemset2DAsync(Q + rk, sizeof(float) * l, 0, sizeof(float) * (l - rk),
+                                           m, s));
+    CSVD_TRY(csvd_gram_apply(Q, l, m, l, blocks, n, Y, l, cuda_stream));
+  }
+  // 3. U_r: the top r left singular vectors of Y
+  CSVD_TRY(csvd_top_basis(&yb, 1, m, r, l, 0, cuda_stream, U, r, &rk));
+  if (rk < r) CUDA_TRY(cudaMemset2DAsync(U + rk, sizeof(float) * r, 0, sizeof(float) * (r - rk), m, s));
+  // 4. the explicit residual energy of U_r
+  std::vector<double> res(n);
+  CSVD_TRY(csvd_tail_energy(U, r, m, r, blocks, n, cuda_stream, res.data()));
+  double t = 0.0;
+  for (double x : res) t += x;
+  *tail_sq = t;
+  if (U_out)
+    CUDA_TRY(cudaMemcpy2DAsync(U_out, sizeof(float) * ldu, U, sizeof(float) * r, sizeof(float) * r,
+                               m, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return CSVD_OK;
 }
 
 extern "C" csvd_status csvd_block_energy(const csvd_block* blocks, int32_t n, int64_t m,

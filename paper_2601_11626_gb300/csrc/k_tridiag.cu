@@ -831,11 +831,11 @@ std::string tridiag_selftest() {
       return "launch class of n = " + std::to_string(n);
   }
   // every core size a class can receive under any tunable edges
-  for (int n = 1; n <= 1024; ++n) for (int cls = 0; cls < 3; ++cls) {
-    const int class_max = cls == 0 ? kEdgeMax[0] : cls == 1 ? kEdgeMax[1] : 1024;
+  for (int n = 1; n <= 1536; ++n) for (int cls = 0; cls < 3; ++cls) {
+    const int class_max = cls == 0 ? kEdgeMax[0] : cls == 1 ? kEdgeMax[1] : 1536;
     const int class_min = cls == 0 ? 1 : kEdgeMin + 1;
     if (n < class_min || n > class_max) continue;
-    for (int n_max = n; n_max <= class_max; n_max += (cls == 2 ? 3 : 1)) {
+    for (int n_max = n; n_max <= class_max; n_max += (cls == 2 ? 5 : 1)) {
       const int smem = tridiag_smem_bytes(cls, n_max);
       if (smem <= 0 || smem > 227 * 1024) {
         snprintf(buf, sizeof buf, "shared memory %d B for class %d, n_max %d", smem, cls, n_max);

@@ -90,6 +90,8 @@ def _sig(lib):
     lib.csvd_tune_set.argtypes = [I32, I32]
     lib.csvd_tail_energy.argtypes = [VP, I64, I64, I32, P(Block), I32, VP, P(D)]
     lib.csvd_top_basis.argtypes = [P(Block), I32, I64, I32, I32, I32, VP, VP, I64, P(I32)]
+    lib.csvd_randomized_tail.argtypes = [P(Block), P(VP), I32, I64, I32, I32, I32, VP, P(D), VP,
+                                         I64]
     lib.csvd_tune_get.argtypes = [P(I32), P(I32)]
     lib.csvd_score_one_noalloc.argtypes = [VP, P(Block), D, VP, VP, VP, VP]
     lib.csvd_score_one_noalloc.restype = C.c_int
@@ -105,7 +107,7 @@ def _sig(lib):
                  "csvd_stream_cluster", "csvd_stream_free",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator",
                  "csvd_debug_limits", "csvd_tune_set", "csvd_tune_get", "csvd_tail_energy",
-                 "csvd_top_basis"):
+                 "csvd_top_basis", "csvd_randomized_tail"):
         getattr(lib, name).restype = C.c_int
 
 
@@ -538,6 +540,27 @@ def residual_energy(U: torch.Tensor, blocks) -> np.ndarray:
     _check(lib().csvd_tail_energy(C.c_void_p(U.data_ptr()), U.stride(0), m, r, _blocks(blocks, m),
                                   len(blocks), _stream(), out))
     return np.frombuffer(out, dtype=np.float64, count=len(blocks)).copy()
+
+
+def randomized_tail(blocks, omegas, r, power_iters=1, want_basis=False):
+    """Randomized range-finder tail estimate (csvd_randomized_tail): the
+    explicit residual energy of the top-r left singular vectors of the
+    sketch sum_i A_i Omega_i after ``power_iters`` power iterations.
+    ``omegas``: CUDA float32 tensors (k_i x l)."""
+    m = blocks[0].shape[0]
+    l = int(omegas[0].shape[1])
+    om = [o.contiguous() for o in omegas]
+    for b, o in zip(blocks, om):
+        if o.shape != (b.shape[1], l) or o.dtype != torch.float32 or not o.is_cuda:
+            raise ValueError("each Omega_i must be a CUDA float32 (k_i x l) tensor")
+    ptrs = (C.c_void_p * len(om))(*[o.data_ptr() for o in om])
+    t = C.c_double()
+    U = torch.empty(m, r, device="cuda", dtype=torch.float32) if want_basis else None
+    _check(lib().csvd_randomized_tail(_blocks(blocks, m), ptrs, len(blocks), m, r, l,
+                                      int(power_iters), _stream(), C.byref(t),
+                                      C.c_void_p(U.data_ptr()) if U is not None else None,
+                                      r))
+    return (t.value, U) if want_basis else t.value
 
 
 class TailEnergy(torch.autograd.Function):

@@ -354,12 +354,16 @@ csvd_status csvd_tune_get(int32_t* edge_small, int32_t* edge_medium);
  * secular-root iteration (solver_iters, default 64; 128 for the FP64
  * re-solve) and the limit of the tensor-core Gram kernel's pipeline waits
  * in ns of device time (wait_ns, default 2e9; the drains after an abort
- * keep the default).  A negative value restores the default.  A cap that is
- * hit surfaces as CSVD_ERR_NOT_CONVERGED, a wait that gives up as
- * CSVD_ERR_TIMEOUT, both at the next synchronising call on the state whose
- * status word the launch used; results of that call are not meaningful.
- * Not thread-safe against concurrent launches. */
-csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns);
+ * keep the default).  A negative value restores the default.  With
+ * stall_gram = 1 the Gram kernel's MMA role first waits on a barrier that
+ * nothing arrives at, so that its bounded wait runs out after wait_ns and
+ * the kernel aborts cleanly (copies drained, TMEM freed); 0 restores normal
+ * operation.  A cap that is hit surfaces as CSVD_ERR_NOT_CONVERGED, a wait
+ * that gives up as CSVD_ERR_TIMEOUT, both at the next synchronising call on
+ * the state whose status word the launch used; results of that call are not
+ * meaningful.  Not thread-safe against concurrent launches. */
+csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns,
+                              int32_t stall_gram);
 
 /* Launch tracing.  csvd_launch_count: kernels launched by this library so
  * far in the process.  csvd_profile(1) clears and starts recording a pair of

@@ -898,12 +898,13 @@ csvd_status csvd_tune_get(int32_t* edge_small, int32_t* edge_medium) {
   return CSVD_OK;
 }
 
-csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns) {
+csvd_status csvd_debug_limits(int32_t jacobi_sweeps, int32_t solver_iters, int64_t wait_ns,
+                              int32_t stall_gram) {
   cudaError_t e = jacobi_set_cap(jacobi_sweeps);
   if (e == cudaSuccess) e = tridiag_set_bisect_cap(solver_iters);
   if (e == cudaSuccess) e = refine64_set_bisect_cap(solver_iters);
   if (e == cudaSuccess) e = arrow_set_cap(solver_iters);
-  if (e == cudaSuccess) e = tc_set_wait_ns(wait_ns);
+  if (e == cudaSuccess) e = tc_set_wait_ns(wait_ns, stall_gram);
   if (e != cudaSuccess) return fail(CSVD_ERR_CUDA, cudaGetErrorString(e));
   return CSVD_OK;
 }

@@ -236,7 +236,7 @@ cudaError_t tridiag_set_bisect_cap(int cap);
 cudaError_t refine64_set_bisect_cap(int cap);
 cudaError_t arrow_set_cap(int cap);
 cudaError_t jacobi_set_cap(int cap);
-cudaError_t tc_set_wait_ns(long long ns);
+cudaError_t tc_set_wait_ns(long long ns, int stall);
 // The mixed core marks an item for the FP64 re-solve when its estimated tail
 // lies below this fraction of the merged energy.
 constexpr double kRefineFrac = 2e-3;

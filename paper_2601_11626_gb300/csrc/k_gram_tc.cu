@@ -26,13 +26,13 @@
 // Structure: persistent CTAs walk a list of 128 x 128 output tiles (tiles of
 // one candidate are adjacent so its columns stay in L2 while they are
 // reused).  Warp roles, connected by mbarrier rings:
-//   warp 0      TMA: up to four boxes per operand per stage into a 3-deep
+//   warp 0      TMA: up to four boxes per operand per stage into a 4-deep
 //               staging ring
 //   warps 2-9   split staging f32 into the bf16 parts of a 2-deep operand
 //               ring; on diagonal tiles also the column sums of squares
 //   warp 1      one thread issues tcgen05.mma (M = 128, K = 16, N = the
 //               tile's valid columns rounded up to 16) into a fresh f32
-//               accumulator per stage (two in TMEM, alternating) and commits
+//               accumulator per stage (kTcXBuf in TMEM, in turn) and commits
 //   warps 10-17 add each stage's accumulator into the tile's running sum
 //               (round to nearest, kept in TMEM) and store the last one;
 //               the tensor cores' own accumulation truncates, so a long
@@ -62,7 +62,10 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 // test hook); the drains after an abort always keep kWaitNs
 __device__ unsigned long long d_wait_ns = kWaitNs;
 // TMEM columns: two stage accumulators X and the running sum S of a tile
-constexpr uint32_t kXCol0 = 0, kSCol0 = 2 * kTcBN, kTmemCols = 512;
+constexpr uint32_t kXCol0 = 0, kSCol0 = kTcXBuf * kTcBN, kTmemCols = 512;
+// failure-path test hook: the MMA role first waits on a barrier nothing
+// arrives at (so the bounded wait runs out); 0 in normal operation
+__device__ int d_stall_test = 0;
 static_assert(kTcConvWarps == 8, "four split warps per 64-column atom");
 
 // kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, both
@@ -321,10 +324,12 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   auto empty_st = [&](int s) { return b0 + 8u * (F + s); };
   auto full_op = [&](int s) { return b0 + 8u * (2 * F + s); };
   auto empty_op = [&](int s) { return b0 + 8u * (2 * F + B + s); };
+  constexpr int X = kTcXBuf;
   auto x_full = [&](int a) { return b0 + 8u * (2 * F + 2 * B + a); };
-  auto x_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + 2 + a); };
-  const uint32_t final_bar = b0 + 8u * (2 * F + 2 * B + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F + 2 * B + 5);
+  auto x_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + X + a); };
+  const uint32_t final_bar = b0 + 8u * (2 * F + 2 * B + 2 * X);
+  const uint32_t stall_bar = b0 + 8u * (2 * F + 2 * B + 2 * X + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F + 2 * B + 2 * X + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -337,11 +342,12 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       mbar_init(full_op(s), kTcConvWarps);
       mbar_init(empty_op(s), 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < X; ++a) {
       mbar_init(x_full(a), 1);
       mbar_init(x_empty(a), kTcEpiWarps);
     }
     mbar_init(final_bar, 1);
+    mbar_init(stall_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -398,6 +404,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
+      if (d_stall_test) ok = mbar_wait(stall_bar, 0u, abort_flag);  // runs out: nothing arrives
       for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
         const TileInfo ti = tile_info(items, tiles[tt]);
         const int nkb = (ti.m + kTcBK - 1) / kTcBK;
@@ -405,8 +412,8 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         const uint32_t idesc = idesc_n(min(kTcBN, (ti.validB + 15) & ~15));
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int slot = it % B;
-          const uint32_t xb = it & 1u;
-          if (!mbar_wait(x_empty(xb), ((it >> 1) & 1u) ^ 1u, abort_flag) ||
+          const uint32_t xb = it % X;
+          if (!mbar_wait(x_empty(xb), ((it / X) & 1u) ^ 1u, abort_flag) ||
               !mbar_wait(full_op(slot), (it / B) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dt = tmem_base + kXCol0 + xb * (uint32_t)kTcBN;
@@ -540,8 +547,8 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       const int nkb = (ti.m + kTcBK - 1) / kTcBK;
       const bool vec = (ti.ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(ti.out) & 15) == 0;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const uint32_t xb = it & 1u;
-        if (!warp_wait(x_full(xb), (it >> 1) & 1u, abort_flag)) { ok = false; break; }
+        const uint32_t xb = it % X;
+        if (!warp_wait(x_full(xb), (it / X) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const bool last = kb + 1 == nkb;
         bool stored = false;
@@ -615,9 +622,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-cudaError_t tc_set_wait_ns(long long ns) {
+cudaError_t tc_set_wait_ns(long long ns, int stall) {
   const unsigned long long v = ns < 0 ? kWaitNs : (unsigned long long)ns;
-  return cudaMemcpyToSymbol(d_wait_ns, &v, sizeof(v));
+  cudaError_t e = cudaMemcpyToSymbol(d_wait_ns, &v, sizeof(v));
+  const int st = stall > 0 ? 1 : 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(d_stall_test, &st, sizeof(int));
+  return e;
 }
 
 bool tc_tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUtensorMap* out) {

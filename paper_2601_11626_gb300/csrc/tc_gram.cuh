@@ -35,7 +35,20 @@ struct TcTile {
 // three bf16 parts of both operands in the MN-major 128-byte-swizzled UMMA
 // layout (two 64-column atoms of kTcBK rows per part).
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32, kTcBox = 32;
-constexpr int kTcStagesF = 3, kTcStagesB = 2;
+// Ring depths: staging slots (F), operand slots (B) and stage accumulators
+// in TMEM (X; the running sum takes one more 128-column buffer, X + 1 <= 4).
+#ifndef CSVD_TC_STAGES_F
+#define CSVD_TC_STAGES_F 4
+#endif
+#ifndef CSVD_TC_STAGES_B
+#define CSVD_TC_STAGES_B 2
+#endif
+#ifndef CSVD_TC_XBUF
+#define CSVD_TC_XBUF 2
+#endif
+constexpr int kTcStagesF = CSVD_TC_STAGES_F, kTcStagesB = CSVD_TC_STAGES_B;
+constexpr int kTcXBuf = CSVD_TC_XBUF;
+static_assert(kTcXBuf >= 2 && kTcXBuf <= 3, "two or three stage accumulators");
 constexpr int kTcConvWarps = 8;  // warps splitting f32 into bf16 parts
 constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter
 constexpr int kTcThreads = (2 + kTcConvWarps + kTcEpiWarps) * 32;
@@ -43,7 +56,8 @@ constexpr int kTcBoxBytes = kTcBK * kTcBox * 4;                 // 4 KB
 constexpr int kTcStageF = 2 * (kTcBM / kTcBox) * kTcBoxBytes;   // 32 KB: A and B, f32
 constexpr int kTcPartBytes = kTcBK * kTcBM * 2;                 // 8 KB: one bf16 part
 constexpr int kTcStageB = 6 * kTcPartBytes;                     // 48 KB: 3 parts x 2 operands
-constexpr int kTcSmemBytes = kTcStagesF * kTcStageF + kTcStagesB * kTcStageB + 2048;
+constexpr int kTcSmemBytes = kTcStagesF * kTcStageF + kTcStagesB * kTcStageB + 1024 + 256;
+static_assert(kTcSmemBytes <= 227 * 1024, "one CTA per SM");
 
 // Encodes the tensor map the kernel expects for a row-major f32 matrix
 // (rows x cols, leading dimension ld floats): box kTcBK rows x kTcBox

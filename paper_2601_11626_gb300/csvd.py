@@ -86,7 +86,7 @@ def _sig(lib):
     lib.csvd_tail_grad.argtypes = [VP, I64, I64, I32, P(Block), P(Block), I32, D, VP]
     lib.csvd_block_energy.argtypes = [P(Block), I32, I64, VP, P(D)]
     lib.csvd_set_allocator.argtypes = [VP, VP, VP]
-    lib.csvd_debug_limits.argtypes = [I32, I32, I64]
+    lib.csvd_debug_limits.argtypes = [I32, I32, I64, I32]
     lib.csvd_tune_set.argtypes = [I32, I32]
     lib.csvd_tail_energy.argtypes = [VP, I64, I64, I32, P(Block), I32, VP, P(D)]
     lib.csvd_top_basis.argtypes = [P(Block), I32, I64, I32, I32, I32, VP, VP, I64, P(I32)]
@@ -589,10 +589,12 @@ def tail_energy(blocks, r, working_rank=None):
     return TailEnergy.apply(r, working_rank, *blocks)
 
 
-def debug_limits(jacobi_sweeps: int = -1, solver_iters: int = -1, wait_ns: int = -1):
-    """Failure-path test hook (csvd_debug_limits): solver caps and the
-    tensor-core pipeline wait limit of the current device; -1 restores."""
-    _check(lib().csvd_debug_limits(jacobi_sweeps, solver_iters, wait_ns))
+def debug_limits(jacobi_sweeps: int = -1, solver_iters: int = -1, wait_ns: int = -1,
+                 stall_gram: bool = False):
+    """Failure-path test hook (csvd_debug_limits): solver caps, the
+    tensor-core pipeline wait limit and its never-arriving barrier, for the
+    current device; -1 / False restore."""
+    _check(lib().csvd_debug_limits(jacobi_sweeps, solver_iters, wait_ns, 1 if stall_gram else 0))
 
 
 def launch_count() -> int:

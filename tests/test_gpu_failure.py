@@ -1,9 +1,10 @@
 """Failure paths, on the GPU, in the forms that fault nothing: an allocator
 that returns NULL, solver iteration caps lowered to zero, and the
-tensor-core kernel's bounded pipeline waits shortened to zero so that they
-give up.  Each surfaces as a status code at the next synchronising call,
-and the library stays usable afterwards (a clean call gives the same
-results as before)."""
+tensor-core kernel's bounded pipeline wait shortened to 2 ms and pointed at
+a barrier that nothing arrives at, so that it runs out and the kernel
+aborts cleanly.  Each surfaces as a status code at the next synchronising
+call, and the library stays usable afterwards (a clean call gives the same
+results as before, up to FP32 rounding)."""
 import ctypes
 
 import numpy as np
@@ -33,6 +34,14 @@ def setup(cuda_lib):
     yield csvd, w, states
     csvd.debug_limits()  # defaults, whatever happened
     csvd.lib().csvd_set_allocator(None, None, None)
+
+
+def _same(got, ref):
+    """Two clean runs agree up to FP32 rounding (the order of atomic sums
+    differs between runs): E~ within the parity tolerance, flags equal."""
+    g, r = got[1], ref[1]
+    assert np.all(np.abs(g - r) <= 2e-4 * r + 1e-6 * np.abs(r).max()), (g, r)
+    assert np.array_equal(got[2], ref[2])
 
 
 def _score(csvd, w, states, form):
@@ -69,8 +78,7 @@ def test_allocator_returning_null_gives_oom(setup):
     assert calls  # the workspace was requested through the callback
     assert lib.csvd_set_allocator(None, None, None) == 0
     got = _score(csvd, w, states, "mixed")
-    np.testing.assert_allclose(got[1], ref[1], rtol=1e-12)
-    assert np.array_equal(got[2], ref[2])
+    _same(got, ref)
     _sync_status(states)
 
 
@@ -88,14 +96,14 @@ def test_zero_iteration_caps_give_not_converged(setup, form, caps):
     csvd.debug_limits()
     got = _score(csvd, w, states, form)
     _sync_status(states)
-    np.testing.assert_allclose(got[1], ref[1], rtol=1e-9)
+    _same(got, ref)
 
 
 def test_pipeline_waits_that_give_up_give_timeout(setup):
     csvd, w, states = setup
     ref = _score(csvd, w, states, "mixed")
     _sync_status(states)
-    csvd.debug_limits(wait_ns=0)
+    csvd.debug_limits(wait_ns=2_000_000, stall_gram=True)   # a barrier nothing arrives at, 2 ms
     _score(csvd, w, states, "mixed")
     with pytest.raises(csvd.CsvdError) as e:
         _sync_status(states)
@@ -103,5 +111,4 @@ def test_pipeline_waits_that_give_up_give_timeout(setup):
     csvd.debug_limits()
     got = _score(csvd, w, states, "mixed")
     _sync_status(states)
-    np.testing.assert_allclose(got[1], ref[1], rtol=1e-9)
-    assert np.array_equal(got[2], ref[2])
+    _same(got, ref)

@@ -11,7 +11,7 @@
 // One CTA per item, in three launch classes by core size: 4 warps (four
 // CTAs per SM) for n <= 192, 8 warps (two per SM) for n <= 320, 16 warps
 // (one per SM) above.  Each CTA owns its SM share of tensor memory (TMEM).
-// Tiles are processed 8 columns at a time.
+// Tiles are processed 16 columns at a time.
 //  1. G is assembled as 32 x 32 tiles of its lower tile triangle (diagonal
 //     tiles hold both halves), listed column by column.  The tiles consumed
 //     last -- revisited by the most steps -- live in TMEM (one tile per
@@ -189,7 +189,7 @@ __device__ __forceinline__ void flush_cols(float2 (&cp)[16], int b, int lane, co
 }
 #undef CP
 
-// Where row `lane` of a tile lives, moved 8 columns at a time.  Shared-memory
+// Where row `lane` of a tile lives, moved 16 columns at a time.  Shared-memory
 // tiles are row-major with 16-byte chunks XOR-swizzled by row (element
 // (i, j) at 32 i + 4 ((j / 4) ^ (i % 8)) + j % 4), so a row moves with
 // conflict-free 128-bit accesses; global tiles are column-major (element
@@ -197,54 +197,77 @@ __device__ __forceinline__ void flush_cols(float2 (&cp)[16], int b, int lane, co
 // i in lane i of the warp's quarter.
 struct SmemTile {
   float* tp;
-  __device__ __forceinline__ void load8(int lane, int k8, float2 (&v)[4]) const {
+  __device__ __forceinline__ void load16(int lane, int k16, float2 (&v)[8]) const {
     const float4* rp = reinterpret_cast<const float4*>(tp + lane * kTile);
-    const float4 x = rp[(2 * k8) ^ (lane & 7)], y = rp[(2 * k8 + 1) ^ (lane & 7)];
-    v[0] = make_float2(x.x, x.y);
-    v[1] = make_float2(x.z, x.w);
-    v[2] = make_float2(y.x, y.y);
-    v[3] = make_float2(y.z, y.w);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 x = rp[(4 * k16 + c) ^ (lane & 7)];
+      v[2 * c] = make_float2(x.x, x.y);
+      v[2 * c + 1] = make_float2(x.z, x.w);
+    }
   }
-  __device__ __forceinline__ void store8(int lane, int k8, const float2 (&v)[4]) const {
+  __device__ __forceinline__ void store16(int lane, int k16, const float2 (&v)[8]) const {
     float4* rp = reinterpret_cast<float4*>(tp + lane * kTile);
-    rp[(2 * k8) ^ (lane & 7)] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    rp[(2 * k8 + 1) ^ (lane & 7)] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      rp[(4 * k16 + c) ^ (lane & 7)] = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
   }
 };
 struct GlobTile {
   float* tp;
-  __device__ __forceinline__ void load8(int lane, int k8, float2 (&v)[4]) const {
+  __device__ __forceinline__ void load16(int lane, int k16, float2 (&v)[8]) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      v[j] = make_float2(tp[(8 * k8 + 2 * j) * kTile + lane], tp[(8 * k8 + 2 * j + 1) * kTile + lane]);
+    for (int j = 0; j < 8; ++j)
+      v[j] = make_float2(tp[(16 * k16 + 2 * j) * kTile + lane], tp[(16 * k16 + 2 * j + 1) * kTile + lane]);
   }
-  __device__ __forceinline__ void store8(int lane, int k8, const float2 (&v)[4]) const {
+  __device__ __forceinline__ void store16(int lane, int k16, const float2 (&v)[8]) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      tp[(8 * k8 + 2 * j) * kTile + lane] = v[j].x;
-      tp[(8 * k8 + 2 * j + 1) * kTile + lane] = v[j].y;
+    for (int j = 0; j < 8; ++j) {
+      tp[(16 * k16 + 2 * j) * kTile + lane] = v[j].x;
+      tp[(16 * k16 + 2 * j + 1) * kTile + lane] = v[j].y;
     }
   }
 };
 struct TmemTile {
   uint32_t taddr;
-  __device__ __forceinline__ void load8(int, int k8, float2 (&v)[4]) const {
-    float x[8];
-    tmem_load8(taddr + 8u * k8, x);
+  __device__ __forceinline__ void load16(int, int k16, float2 (&v)[8]) const {
+    uint32_t r[16];
+    tmem_load16(taddr + 16u * k16, r);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = make_float2(x[2 * j], x[2 * j + 1]);
+    for (int j = 0; j < 8; ++j) v[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
   }
-  __device__ __forceinline__ void store8(int, int k8, const float2 (&v)[4]) const {
-    const float x[8] = {v[0].x, v[0].y, v[1].x, v[1].y, v[2].x, v[2].y, v[3].x, v[3].y};
-    tmem_store8(taddr + 8u * k8, x);
+  __device__ __forceinline__ void store16(int, int k16, const float2 (&v)[8]) const {
+    uint32_t r[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { r[2 * j] = __float_as_uint(v[j].x); r[2 * j + 1] = __float_as_uint(v[j].y); }
+    tmem_store16(taddr + 16u * k16, r);
   }
 };
+
+// Columns 16 k16 .. 16 k16 + 15 of the K tiles into registers (a TMEM pair:
+// both loads before one wait).
+template <int K, class Tile>
+__device__ __forceinline__ void load_group(const Tile (&tl)[K], int lane, int k16, float2 (&v)[K][8]) {
+#pragma unroll
+  for (int t = 0; t < K; ++t) tl[t].load16(lane, k16, v[t]);
+}
+template <>
+__device__ __forceinline__ void load_group<2, TmemTile>(const TmemTile (&tl)[2], int, int k16,
+                                                        float2 (&v)[2][8]) {
+  uint32_t r[16], q[16];
+  tmem_load16x2(tl[0].taddr + 16u * k16, tl[1].taddr + 16u * k16, r, q);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[0][j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+    v[1][j] = make_float2(__uint_as_float(q[2 * j]), __uint_as_float(q[2 * j + 1]));
+  }
+}
 
 __device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
   return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
 }
 
-// K tiles of one tile column b (rows a, a + 1, ...), 8 columns at a time:
+// K tiles of one tile column b (rows a, a + 1, ...), 16 columns at a time:
 // G -= vp wp^T + wp vp^T, row sums (two partial chains per tile, added to
 // p[row]) and column sums (kept in cp across the tiles of the column),
 // column s + 1 and G(n-1, n-1) copied out.  Pairs of columns go through
@@ -273,13 +296,12 @@ __device__ __forceinline__ void process_tiles(const Tile (&tl)[K], int a, int b,
   const float4* wp4 = reinterpret_cast<const float4*>(st.wprev + b * kTile);
   const bool col_next = b == st.b0;  // this tile column holds column s + 1
 #pragma unroll
-  for (int k8 = 0; k8 < 4; ++k8) {
-    float2 v[K][4];
+  for (int k16 = 0; k16 < 2; ++k16) {
+    float2 v[K][8];
+    load_group<K>(tl, lane, k16, v);
 #pragma unroll
-    for (int t = 0; t < K; ++t) tl[t].load8(lane, k8, v[t]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int q4 = 2 * k8 + h;
+    for (int h = 0; h < 4; ++h) {
+      const int q4 = 4 * k16 + h;
       const float4 vc = vc4[q4], vp = vp4[q4], wp = wp4[q4];
       const float2 vc0 = make_float2(vc.x, vc.y), vc1 = make_float2(vc.z, vc.w);
       const float2 vp0 = make_float2(vp.x, vp.y), vp1 = make_float2(vp.z, vp.w);
@@ -301,17 +323,17 @@ __device__ __forceinline__ void process_tiles(const Tile (&tl)[K], int a, int b,
     }
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-      tl[t].store8(lane, k8, v[t]);
+      tl[t].store16(lane, k16, v[t]);
       if (col_next) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          cx[t] = (8 * k8 + j == st.ccn) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x) : cx[t];
+        for (int j = 0; j < 16; ++j)
+          cx[t] = (16 * k16 + j == st.ccn) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x) : cx[t];
       }
       if (last_tile[t]) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          gx[t] = (8 * k8 + j == (st.last_r & 31)) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x)
-                                                   : gx[t];
+        for (int j = 0; j < 16; ++j)
+          gx[t] = (16 * k16 + j == (st.last_r & 31)) ? ((j & 1) ? v[t][j >> 1].y : v[t][j >> 1].x)
+                                                    : gx[t];
       }
     }
   }
@@ -392,19 +414,19 @@ __device__ __forceinline__ void tmem_tiles(uint32_t tq, int q, int ja, int jb, i
   }
 }
 
-// Assemble tile (a, b) of G into its place, 8 columns at a time.
+// Assemble tile (a, b) of G into its place, 16 columns at a time.
 template <class Tile>
 __device__ __forceinline__ void assemble_tile(const Tile& tl, const CoreDesc& d, int n, int a,
                                               int b, int lane) {
   const int r = a * kTile + lane;
 #pragma unroll
-  for (int k8 = 0; k8 < 4; ++k8) {
-    float2 v[4];
+  for (int k16 = 0; k16 < 2; ++k16) {
+    float2 v[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      v[j] = make_float2(core_gram(d, n, r, b * kTile + 8 * k8 + 2 * j),
-                         core_gram(d, n, r, b * kTile + 8 * k8 + 2 * j + 1));
-    tl.store8(lane, k8, v);
+    for (int j = 0; j < 8; ++j)
+      v[j] = make_float2(core_gram(d, n, r, b * kTile + 16 * k16 + 2 * j),
+                         core_gram(d, n, r, b * kTile + 16 * k16 + 2 * j + 1));
+    tl.store16(lane, k16, v);
   }
 }
 

@@ -73,27 +73,42 @@ __device__ __forceinline__ void tmem_store_tile(uint32_t taddr, const float* v) 
       : "memory");
 }
 
-// 8-column variants: lane i <-> columns [col, col + 8) of TMEM lane base + i.
-// The load waits for itself inside the same statement, so its outputs exist
-// only once they are valid; neither touches generic memory, so the compiler
-// may move shared- or global-memory accesses across them (the relative order
-// of tcgen05 statements, fences and barriers is kept: all are volatile).
-__device__ __forceinline__ void tmem_load8(uint32_t taddr, float* v) {
-  uint32_t r[8];
+// 16-column variants: lane i <-> columns [col, col + 16) of TMEM lane base + i.
+// A load waits for itself inside the same statement, so its outputs exist
+// only once they are valid (the paired load issues both tiles' loads before
+// its one wait); neither loads nor stores touch generic memory, so the
+// compiler may move shared- or global-memory accesses across them (the
+// relative order of tcgen05 statements, fences and barriers is kept: all are
+// volatile).
+#define CSVD_R16(o) "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), \
+    "=r"(o[6]), "=r"(o[7]), "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]),  \
+    "=r"(o[13]), "=r"(o[14]), "=r"(o[15])
+__device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
+      : CSVD_R16(r)
       : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_store8(uint32_t taddr, const float* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
+__device__ __forceinline__ void tmem_load16x2(uint32_t ta, uint32_t tb, uint32_t (&r)[16],
+                                              uint32_t (&q)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+      "%28,%29,%30,%31}, [%33];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : CSVD_R16(r), CSVD_R16(q)
+      : "r"(ta), "r"(tb));
+}
+#undef CSVD_R16
+__device__ __forceinline__ void tmem_store16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
 }
 
 }  // namespace csvd

@@ -636,6 +636,8 @@ def main():
     ap.add_argument("--leg-steps", type=int, default=3)
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="keep the hand-set launch classes of the eigen core")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="skip the CUDA-graph replay of the step")
     ap.add_argument("--e2e-steps", type=int, default=20,
                     help="end-to-end steps; the first copy cannot overlap a step, so more "
                          "steps weigh the pipeline fill less")
@@ -701,8 +703,13 @@ def main():
         tuning = tune.autotune(batch, [ranks[w["cand_state"][i]] + cands[i].shape[1]
                                        for i in range(n)], m, ranks, steps=2)
         tuning["edges"] = list(tuning["edges"])
+    # the step as a prepared plan (csvd_score_plan): descriptors, tile lists
+    # and workspace built once after the tuning; every step then launches
+    # the same kernels on the resident candidates
+    batch.plan()
     for _ in range(args.warmup):
-        batch.run()
+        batch.launch()
+    batch.check()
     barrier()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -711,15 +718,35 @@ def main():
         l0 = csvd.launch_count()
         e0.record(stream)
         for _ in range(args.steps):
-            batch.run()
+            batch.launch()
         e1.record(stream)
         e1.synchronize()
         launches = csvd.launch_count() - l0
         prof = csvd.profile_report()
         csvd.profile(False)
+    batch.check()
     ms = e0.elapsed_time(e1)
     barrier()
     value, ms = job_throughput(ms, n * args.steps, world)
+
+    # the same step captured once into a CUDA graph and replayed
+    graph = None
+    if args.graph:
+        g = batch.graph()
+        for _ in range(args.warmup):
+            g.replay()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        g1.record(stream)
+        g1.synchronize()
+        batch.check()
+        gv, gms = job_throughput(g0.elapsed_time(g1), n * args.steps, world)
+        graph = {"value": gv, "unit": UNIT, "ms_per_step": gms / args.steps, "steps": args.steps,
+                 "kernels_per_step": launches // max(args.steps, 1)}
+        del g
 
     # dominant kernel roofline
     peaks, peak_src = _peaks()
@@ -800,7 +827,7 @@ def main():
             return out
 
         batches = [batch, csvd.ScoreBatch(states, w["cand_state"], views(pools[1]), eps,
-                                          args.precision)]
+                                          args.precision).plan()]
         out_bytes = batch.tail.numel() * 8 + batch.accept.numel() + batch.sigma.numel() * 4
         outs = [(torch.empty(batch.tail.shape, dtype=batch.tail.dtype, pin_memory=True),
                  torch.empty(batch.accept.shape, dtype=batch.accept.dtype, pin_memory=True),
@@ -834,12 +861,14 @@ def main():
                 c1[i].record(copy_stream)
                 ready[b].record(copy_stream)
             stream.wait_event(ready[b])
-            batches[b].run()
+            batches[b].launch()
             for o, src in zip(outs[b], (batches[b].tail, batches[b].accept, batches[b].sigma)):
                 o.copy_(src, non_blocking=True)
             done[b].record(stream)
         q1.record(stream)
         q1.synchronize()
+        for bt in batches:
+            bt.check()
         qms = q0.elapsed_time(q1) / args.e2e_steps
         h2d_ms = sum(a.elapsed_time(z) for a, z in zip(c0, c1)) / args.e2e_steps
         e2e_value, qms = job_throughput(qms, n, world)
@@ -851,6 +880,7 @@ def main():
                "h2d_gbs_alone": in_bytes / (alone_ms / 1000.0) / 1e9,
                "h2d_ms_each": [round(a.elapsed_time(z), 2) for a, z in zip(c0, c1)],
                "overlap": "inputs of step i copied on a second stream while step i-1 is scored"}
+        batches[1].close()
         del batches, pools
 
     # sampled parity against the FP64 oracle from the states the GPU used
@@ -910,6 +940,7 @@ def main():
                 "precision_form": args.precision, "eps": eps,
                 "l2": "inputs (%.1f GB) larger than L2, no flush" % (pool_bytes / 1e9),
                 "parallelism": f"dp{world} (candidates sharded, no collective on the data path)"},
+            "graph": graph,
             "plain_fp32": plain, "plain_fp32_jacobi": jacobi, "parity": parity, "e2e": e2e,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": launches, "legs": legs, "tuning": tuning,

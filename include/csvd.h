@@ -144,6 +144,42 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
                        float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
                        double* tail_paper_out, uint8_t* accept_out);
 
+/* Prepared batched merge evaluation: the same evaluation as csvd_score
+ * (same arguments and outputs, Alg. 3 step 3(a)-(e)), split into a set-up
+ * that does all host work once -- argument checks, descriptors, tile lists,
+ * TMA tensor maps, the workspace (from the installed allocator) and its
+ * upload; it syncs the stream of states[0] before returning -- and
+ * csvd_plan_launch, which only enqueues memsets and kernel launches.  The
+ * plan keeps the device addresses of the states' bases, singular values
+ * and energies, of the candidate blocks and of the outputs: while it lives
+ * no state may be appended to, loaded or freed and every buffer must stay
+ * allocated (their contents may change between launches: a launch reads
+ * whatever the blocks hold when it runs).  The paper has no counterpart; it
+ * serves repeated evaluation of fixed candidate sets and CUDA graphs.
+ * Errors: as csvd_score (nothing is allocated on failure). */
+typedef struct csvd_plan_s* csvd_plan;
+csvd_status csvd_score_plan(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
+                            const csvd_block* cands, int32_t n, double eps, int32_t precision,
+                            float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                            double* tail_paper_out, uint8_t* accept_out, csvd_plan* out);
+
+/* Enqueue one evaluation of the plan on cuda_stream (NULL: the stream of
+ * states[0] at set-up): memsets and kernel launches only, no allocation,
+ * host copy or synchronisation, so the call can be captured into a CUDA
+ * graph (after one launch outside the capture, which sets the kernels'
+ * shared-memory limits).  Launches of one plan share its workspace: order
+ * them on one stream.  Device-side failures (caps, bounded waits) are
+ * recorded in the plan's status word, read by csvd_plan_status. */
+csvd_status csvd_plan_launch(csvd_plan p, void* cuda_stream);
+
+/* Synchronise cuda_stream (NULL: the set-up stream), then read and clear
+ * the plan's status word: CSVD_ERR_NOT_CONVERGED, CSVD_ERR_TIMEOUT or
+ * CSVD_ERR_SHAPE for failures recorded since the last read. */
+csvd_status csvd_plan_status(csvd_plan p, void* cuda_stream);
+
+/* Release the plan and its workspace (synchronises the device first). */
+csvd_status csvd_plan_free(csvd_plan p);
+
 /* Batched merge evaluation of one-column candidates (blocks of width 1,
  * the k = 1 regime of the evaluation section's dataset table) given as the
  * rows of one matrix: candidate j is the column a_j = Xt[j * ldx + i],

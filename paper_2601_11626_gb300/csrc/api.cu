@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -132,6 +133,27 @@ struct Workspace {
   T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
 
+// The stream work of a prepared batched evaluation (csvd_score_plan): memsets
+// and kernel launches on device buffers the plan owns, replayed by
+// csvd_plan_launch without any allocation, host copy or synchronisation.
+using StreamOp = std::function<cudaError_t(cudaStream_t)>;
+struct LaunchPlan {
+  std::vector<StreamOp> ops;
+  std::vector<void*> bufs;   // device buffers the ops use (freed with the plan)
+  cudaStream_t s = nullptr;  // stream the plan was built on
+  int* status = nullptr;     // its device status word (in bufs)
+};
+
+// Runs the stream work now, or appends it to a plan.
+static csvd_status run_or_keep(std::vector<StreamOp>& ops, cudaStream_t s, LaunchPlan* plan) {
+  if (plan) {
+    for (auto& op : ops) plan->ops.push_back(std::move(op));
+    return CSVD_OK;
+  }
+  for (auto& op : ops) CUDA_TRY(op(s));
+  return CSVD_OK;
+}
+
 // Pinned host staging ring for descriptor uploads.
 struct StagingRing {
   struct Slot {
@@ -211,6 +233,16 @@ struct GemmBatch {
     if (tiles.empty()) return cudaSuccess;
     return launch_gemm(reinterpret_cast<const GemmDesc*>(dbase + off_d),
                        reinterpret_cast<const GemmTile*>(dbase + off_t), (int)tiles.size(), s);
+  }
+  // the launch as a stream operation (captures offsets and counts only)
+  StreamOp op(char* dbase) const {
+    const size_t d = off_d, t = off_t;
+    const int nt = (int)tiles.size();
+    return [=](cudaStream_t st) {
+      if (nt == 0) return cudaSuccess;
+      return launch_gemm(reinterpret_cast<const GemmDesc*>(dbase + d),
+                         reinterpret_cast<const GemmTile*>(dbase + t), nt, st);
+    };
   }
 };
 
@@ -401,7 +433,7 @@ static void arrow_item_groups(const std::vector<Item>& items, std::vector<int>& 
 }
 
 static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, cudaStream_t s,
-                                   int* d_status) {
+                                   int* d_status, LaunchPlan* plan = nullptr) {
   const int n = (int)items.size();
   if (n == 0) return CSVD_OK;
   std::vector<int> order;
@@ -436,33 +468,45 @@ static csvd_status run_arrow_items(const std::vector<Item>& items, double eps, c
   w.base = static_cast<char*>(dev_alloc(host.size(), s));
   if (!w.base) return fail(CSVD_ERR_OOM, "workspace allocation failed");
   CUDA_TRY(upload(w.base, host.data(), host.size(), s));
-  CUDA_TRY(launch_core_arrow(w.at<ArrowDesc>(0), w.at<int2>(desc_bytes), (int)groups.size(),
-                             d_status, s));
+  std::vector<StreamOp> ops;
+  {
+    ArrowDesc* dd = w.at<ArrowDesc>(0);
+    int2* dg = w.at<int2>(desc_bytes);
+    const int ng = (int)groups.size();
+    ops.push_back([=](cudaStream_t st) { return launch_core_arrow(dd, dg, ng, d_status, st); });
+  }
+  CSVD_TRY(run_or_keep(ops, s, plan));
+  if (plan) {
+    plan->bufs.push_back(w.base);  // the plan owns the descriptors now
+    w.base = nullptr;
+  }
   return CSVD_OK;
 }
 
 static csvd_status run_items_general(const std::vector<Item>& items, double eps, int precision,
                                      cudaStream_t s, int* d_status, Workspace& ws,
-                                     CommitKeep* keep, bool want_W);
+                                     CommitKeep* keep, bool want_W, LaunchPlan* plan = nullptr);
 
+// With a plan, the stream work is kept in it (and the buffers it uses move
+// into it) instead of running.
 static csvd_status run_items(const std::vector<Item>& items, double eps, int precision,
                              cudaStream_t s, int* d_status, Workspace& ws, CommitKeep* keep,
-                             bool want_W) {
+                             bool want_W, LaunchPlan* plan = nullptr) {
   if (precision != CSVD_PLAIN_FP32 && !want_W) {
     std::vector<Item> arrow, rest;
     for (const Item& it : items) (arrow_eligible(it) ? arrow : rest).push_back(it);
     if (!arrow.empty()) {
-      CSVD_TRY(run_arrow_items(arrow, eps, s, d_status));
+      CSVD_TRY(run_arrow_items(arrow, eps, s, d_status, plan));
       return rest.empty() ? CSVD_OK : run_items_general(rest, eps, precision, s, d_status, ws, keep,
-                                                        want_W);
+                                                        want_W, plan);
     }
   }
-  return run_items_general(items, eps, precision, s, d_status, ws, keep, want_W);
+  return run_items_general(items, eps, precision, s, d_status, ws, keep, want_W, plan);
 }
 
 static csvd_status run_items_general(const std::vector<Item>& items, double eps, int precision,
                                      cudaStream_t s, int* d_status, Workspace& ws,
-                                     CommitKeep* keep, bool want_W) {
+                                     CommitKeep* keep, bool want_W, LaunchPlan* plan) {
   const int n = (int)items.size();
   if (n == 0) return CSVD_OK;
   Layout L;
@@ -726,13 +770,22 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
   const size_t o_ti = pk.add(tci), o_tt = pk.add(tct);
   char* dbase = ws.base + off_desc;
   CUDA_TRY(upload(dbase, pk.buf.data(), pk.buf.size(), s));
+  // from here on stream work only (memsets and launches on the workspace):
+  // run now, or kept as a plan's operations
+  std::vector<StreamOp> ops;
+  char* wb = ws.base;
   // block energies start at zero (the mixed form sums its column energies)
-  if (!mixed) CUDA_TRY(cudaMemsetAsync(ws.base + energies, 0, sizeof(double) * (size_t)n, s));
-  if (mixed) {
-    CUDA_TRY(cudaMemsetAsync(ws.base + colE_base, 0, sizeof(double) * colE_total, s));
-    CUDA_TRY(cudaMemsetAsync(ws.base + refine_flags, 0, (size_t)n, s));
-    CUDA_TRY(cudaMemsetAsync(ws.base + refine_ctr, 0, sizeof(int), s));
-  }
+  if (!mixed)
+    ops.push_back([=](cudaStream_t st) {
+      return cudaMemsetAsync(wb + energies, 0, sizeof(double) * (size_t)n, st);
+    });
+  if (mixed)
+    ops.push_back([=](cudaStream_t st) {
+      cudaError_t e = cudaMemsetAsync(wb + colE_base, 0, sizeof(double) * colE_total, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(wb + refine_flags, 0, (size_t)n, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(wb + refine_ctr, 0, sizeof(int), st);
+      return e;
+    });
   int max_chunks = 1;
   int max_m = 1;
   for (int i = 0; i < n; ++i) {
@@ -740,33 +793,48 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
     max_chunks = std::max<int>(max_chunks, (int)std::min<int64_t>(64, (tot + 8191) / 8192));
     max_m = std::max<int>(max_m, (int)items[i].m);
   }
-  if (!mixed) CUDA_TRY(launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, s));
-  CUDA_TRY(gP.launch(dbase, s));
+  if (!mixed)
+    ops.push_back([=](cudaStream_t st) {
+      return launch_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ed), n, max_chunks, st);
+    });
+  ops.push_back(gP.op(dbase));
   if (mixed) {
     int max_k = 1;
     for (const EnergyDesc& e : ced) max_k = std::max(max_k, e.k);
-    CUDA_TRY(launch_col_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ce), (int)ced.size(), max_k,
-                               max_m, s));
-    CUDA_TRY(launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti), reinterpret_cast<TcTile*>(dbase + o_tt),
-                            (int)tct.size(), num_sms(), d_status, s));
-    CUDA_TRY(gG.launch(dbase, s));
-    CUDA_TRY(launch_core_tridiag(2, reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
-                                 tri_nmax[2], d_status, s));
-    CUDA_TRY(launch_core_tridiag(1, reinterpret_cast<CoreDesc*>(dbase + o_cm), (int)cd_m.size(),
-                                 tri_nmax[1], d_status, s));
-    CUDA_TRY(launch_core_tridiag(0, reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
-                                 tri_nmax[0], d_status, s));
-    CUDA_TRY(launch_core_refine64(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(),
-                                  reinterpret_cast<CoreDesc*>(dbase + o_cm), (int)cd_m.size(),
-                                  reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(),
-                                  reinterpret_cast<double*>(ws.base + refine_work), refine_slots,
-                                  refine_nmax, reinterpret_cast<int*>(ws.base + refine_ctr),
-                                  d_status, s));
+    const int n_ce = (int)ced.size(), n_tt = (int)tct.size(), n_sms = num_sms();
+    const int n_g = (int)cd_g.size(), n_m = (int)cd_m.size(), n_s = (int)cd_s.size();
+    const int nx0 = tri_nmax[0], nx1 = tri_nmax[1], nx2 = tri_nmax[2];
+    ops.push_back([=](cudaStream_t st) {
+      return launch_col_energy(reinterpret_cast<EnergyDesc*>(dbase + o_ce), n_ce, max_k, max_m, st);
+    });
+    ops.push_back([=](cudaStream_t st) {
+      return launch_tc_gram(reinterpret_cast<TcItem*>(dbase + o_ti),
+                            reinterpret_cast<TcTile*>(dbase + o_tt), n_tt, n_sms, d_status, st);
+    });
+    ops.push_back(gG.op(dbase));
+    ops.push_back([=](cudaStream_t st) {
+      cudaError_t e = launch_core_tridiag(2, reinterpret_cast<CoreDesc*>(dbase + o_cg), n_g, nx2,
+                                          d_status, st);
+      if (e == cudaSuccess)
+        e = launch_core_tridiag(1, reinterpret_cast<CoreDesc*>(dbase + o_cm), n_m, nx1, d_status, st);
+      if (e == cudaSuccess)
+        e = launch_core_tridiag(0, reinterpret_cast<CoreDesc*>(dbase + o_cs), n_s, nx0, d_status, st);
+      if (e == cudaSuccess)
+        e = launch_core_refine64(reinterpret_cast<CoreDesc*>(dbase + o_cg), n_g,
+                                 reinterpret_cast<CoreDesc*>(dbase + o_cm), n_m,
+                                 reinterpret_cast<CoreDesc*>(dbase + o_cs), n_s,
+                                 reinterpret_cast<double*>(wb + refine_work), refine_slots,
+                                 refine_nmax, reinterpret_cast<int*>(wb + refine_ctr), d_status, st);
+      return e;
+    });
   } else {
-    CUDA_TRY(gR.launch(dbase, s));
-    CUDA_TRY(gP2.launch(dbase, s));
-    CUDA_TRY(gRu.launch(dbase, s));
-    CUDA_TRY(launch_householder_qr(reinterpret_cast<QRDesc*>(dbase + o_qd), (int)qd.size(), max_m, s));
+    ops.push_back(gR.op(dbase));
+    ops.push_back(gP2.op(dbase));
+    ops.push_back(gRu.op(dbase));
+    const int n_qd = (int)qd.size();
+    ops.push_back([=](cudaStream_t st) {
+      return launch_householder_qr(reinterpret_cast<QRDesc*>(dbase + o_qd), n_qd, max_m, st);
+    });
     int sm = 0;
     for (auto& c : cd_s) {
       const int nc = c.rt + c.k, nr = c.rt + c.kp;
@@ -774,8 +842,19 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
     }
     int gm = 0;
     for (auto& c : cd_g) gm = std::max(gm, jacobi_scratch_floats(c.rt + c.k) * 4);
-    CUDA_TRY(launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cs), (int)cd_s.size(), sm, d_status, s));
-    CUDA_TRY(launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cg), (int)cd_g.size(), gm, d_status, s));
+    const int n_s = (int)cd_s.size(), n_g = (int)cd_g.size();
+    ops.push_back([=](cudaStream_t st) {
+      cudaError_t e = launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cs), n_s, sm, d_status, st);
+      if (e == cudaSuccess)
+        e = launch_core_jacobi(reinterpret_cast<CoreDesc*>(dbase + o_cg), n_g, gm, d_status, st);
+      return e;
+    });
+  }
+  CSVD_TRY(run_or_keep(ops, s, plan));
+  if (plan) {
+    plan->bufs.push_back(ws.base);  // the plan owns the workspace now
+    ws.base = nullptr;
+    return CSVD_OK;
   }
   if (keep && n == 1 && !mixed) {
     keep->Rt = ws.at<float>(off[0].Rt);
@@ -1026,18 +1105,21 @@ csvd_status csvd_tail_error(csvd_state st, double* tail_sq, double* tail_rel,
   return CSVD_OK;
 }
 
-csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
-                       const csvd_block* cands, int32_t n, double eps, int32_t precision,
-                       float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
-                       double* tail_paper_out, uint8_t* accept_out) {
+}  // extern "C"
+
+// Items of a batched evaluation (csvd_score's arguments, checked).
+static csvd_status score_items(const csvd_state* states, int32_t n_states,
+                               const int32_t* cand_state, const csvd_block* cands, int32_t n,
+                               int32_t precision, float* sigma_out, int64_t ld_sigma,
+                               double* tail_sq_out, double* tail_paper_out, uint8_t* accept_out,
+                               std::vector<Item>& items) {
   if (!states || n_states < 1 || !cands || n < 0 || !sigma_out || !tail_sq_out)
     return fail(CSVD_ERR_ARG, "NULL argument");
   if (precision != CSVD_PLAIN_FP32 && precision != CSVD_MIXED && precision != CSVD_GRAM_FP32)
     return fail(CSVD_ERR_ARG, "bad precision");
-  if (n == 0) return CSVD_OK;
+  if (!states[0]) return fail(CSVD_ERR_ARG, "state 0 is NULL");
   const int64_t m = states[0]->m;
-  cudaStream_t s = states[0]->stream;
-  std::vector<Item> items(n);
+  items.resize(n);
   for (int i = 0; i < n; ++i) {
     const int si = cand_state ? cand_state[i] : 0;
     if (si < 0 || si >= n_states || !states[si]) return fail(CSVD_ERR_ARG, "bad cand_state");
@@ -1048,8 +1130,87 @@ csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t
                     tail_sq_out + i, tail_paper_out ? tail_paper_out + i : nullptr, nullptr,
                     accept_out ? accept_out + i : nullptr};
   }
+  return CSVD_OK;
+}
+
+struct csvd_plan_s {
+  LaunchPlan lp;
+};
+
+static void plan_release(csvd_plan_s* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  for (void* b : p->lp.bufs) dev_free(b, p->lp.s);
+  cudaStreamSynchronize(p->lp.s);
+  delete p;
+}
+
+extern "C" {
+
+csvd_status csvd_score(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
+                       const csvd_block* cands, int32_t n, double eps, int32_t precision,
+                       float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                       double* tail_paper_out, uint8_t* accept_out) {
+  std::vector<Item> items;
+  CSVD_TRY(score_items(states, n_states, cand_state, cands, n, precision, sigma_out, ld_sigma,
+                       tail_sq_out, tail_paper_out, accept_out, items));
+  if (n == 0) return CSVD_OK;
   Workspace ws;
-  return run_items(items, eps, precision, s, states[0]->status, ws, nullptr, false);
+  return run_items(items, eps, precision, states[0]->stream, states[0]->status, ws, nullptr, false);
+}
+
+csvd_status csvd_score_plan(const csvd_state* states, int32_t n_states, const int32_t* cand_state,
+                            const csvd_block* cands, int32_t n, double eps, int32_t precision,
+                            float* sigma_out, int64_t ld_sigma, double* tail_sq_out,
+                            double* tail_paper_out, uint8_t* accept_out, csvd_plan* out) {
+  if (!out) return fail(CSVD_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  std::vector<Item> items;
+  CSVD_TRY(score_items(states, n_states, cand_state, cands, n, precision, sigma_out, ld_sigma,
+                       tail_sq_out, tail_paper_out, accept_out, items));
+  cudaStream_t s = states[0]->stream;
+  auto* p = new csvd_plan_s;
+  p->lp.s = s;
+  p->lp.status = static_cast<int*>(dev_alloc(sizeof(int), s));
+  if (!p->lp.status) {
+    delete p;
+    return fail(CSVD_ERR_OOM, "plan status allocation failed");
+  }
+  p->lp.bufs.push_back(p->lp.status);
+  csvd_status st = CSVD_OK;
+  if (cudaMemsetAsync(p->lp.status, 0, sizeof(int), s) != cudaSuccess)
+    st = fail(CSVD_ERR_CUDA, "plan status memset failed");
+  if (st == CSVD_OK && n > 0) {
+    Workspace ws;
+    st = run_items(items, eps, precision, s, p->lp.status, ws, nullptr, false, &p->lp);
+  }
+  if (st == CSVD_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = fail(CSVD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if (st != CSVD_OK) {
+    plan_release(p);
+    return st;
+  }
+  *out = p;
+  return CSVD_OK;
+}
+
+csvd_status csvd_plan_launch(csvd_plan p, void* cuda_stream) {
+  if (!p) return fail(CSVD_ERR_ARG, "plan is NULL");
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->lp.s;
+  for (auto& op : p->lp.ops) CUDA_TRY(op(s));
+  return CSVD_OK;
+}
+
+csvd_status csvd_plan_status(csvd_plan p, void* cuda_stream) {
+  if (!p) return fail(CSVD_ERR_ARG, "plan is NULL");
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->lp.s;
+  return take_status(p->lp.status, s);
+}
+
+csvd_status csvd_plan_free(csvd_plan p) {
+  if (!p) return fail(CSVD_ERR_ARG, "plan is NULL");
+  plan_release(p);
+  return CSVD_OK;
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 // and ranks (the uneven batches of batched merge scoring).
 #pragma once
 
+#include <atomic>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -184,6 +185,22 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 __device__ __forceinline__ float load_elem(const void* p, int64_t idx, int bf16) {
   if (bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]);
   return reinterpret_cast<const float*>(p)[idx];
+}
+
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than
+// any earlier one (one device per process), so that repeated launches make
+// no attribute call -- a launch-only path can then be captured into a CUDA
+// graph after one launch outside the capture.
+template <class Kernel>
+cudaError_t ensure_smem(Kernel* kernel, int bytes, std::atomic<int>& set_bytes) {
+  if (bytes <= 48 * 1024 || bytes <= set_bytes.load(std::memory_order_relaxed)) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  int cur = set_bytes.load(std::memory_order_relaxed);
+  while (bytes > cur && !set_bytes.compare_exchange_weak(cur, bytes)) {
+  }
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------- launch tracing

@@ -325,11 +325,8 @@ int jacobi_scratch_floats(int nc) {
 cudaError_t launch_core_jacobi(const CoreDesc* d_desc, int n_items, int smem_bytes,
                                int* d_status, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (smem_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_jacobi_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-  }
+  static std::atomic<int> set_smem{0};
+  if (cudaError_t e = ensure_smem(core_jacobi_kernel, smem_bytes, set_smem)) return e;
   prof_begin(s);
   core_jacobi_kernel<<<n_items, 1024, smem_bytes, s>>>(d_desc, d_status);
   prof_end("core_jacobi", s);

@@ -647,10 +647,8 @@ bool tc_tensor_map(const void* ptr, int64_t cols, int64_t rows, int64_t ld, CUte
 cudaError_t launch_tc_gram(const TcItem* d_items, const TcTile* d_tiles, int n_tiles, int n_ctas,
                            int* d_status, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
-  // per device and cheap: set on every launch
-  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kTcSmemBytes);
-  if (e != cudaSuccess) return e;
+  static std::atomic<int> set_smem{0};
+  if (cudaError_t e = ensure_smem(tc_gram_kernel, kTcSmemBytes, set_smem)) return e;
   if (n_ctas > n_tiles) n_ctas = n_tiles;
   prof_begin(s);
   tc_gram_kernel<<<n_ctas, kTcThreads, kTcSmemBytes, s>>>(d_items, d_tiles, n_tiles, d_status);

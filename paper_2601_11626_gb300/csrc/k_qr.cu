@@ -75,11 +75,8 @@ cudaError_t launch_householder_qr(const QRDesc* d_desc, int n_items, int max_m,
                                   cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   const int smem = (max_m + 40) * (int)sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(householder_qr_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
+  static std::atomic<int> set_smem{0};
+  if (cudaError_t e = ensure_smem(householder_qr_kernel, smem, set_smem)) return e;
   prof_begin(s);
   householder_qr_kernel<<<n_items, 512, smem, s>>>(d_desc);
   prof_end("householder_qr", s);

@@ -232,11 +232,8 @@ cudaError_t launch_core_refine64(const CoreDesc* d0, int n0, const CoreDesc* d1,
                                  int* d_counter, int* d_status, cudaStream_t s) {
   if (n0 + n1 + n2 <= 0 || slots <= 0) return cudaSuccess;
   const size_t smem = refine64_smem_bytes(n_max);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_refine64_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static std::atomic<int> set_smem{0};
+  if (cudaError_t e = ensure_smem(core_refine64_kernel, (int)smem, set_smem)) return e;
   prof_begin(s);
   core_refine64_kernel<<<slots, kThreads, smem, s>>>(d0, n0, d1, n1, d2, n2, work, n_max,
                                                      d_counter, d_status);

@@ -825,11 +825,8 @@ int64_t tridiag_work_floats(int cls, int n, int n_max) {
 template <int kCls>
 static cudaError_t launch_class(const CoreDesc* d_desc, int n_items, int smem_bytes, int n_max,
                                 int* d_status, cudaStream_t s) {
-  if (smem_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(core_tridiag_kernel<kCls>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-  }
+  static std::atomic<int> set_smem{0};
+  if (cudaError_t e = ensure_smem(core_tridiag_kernel<kCls>, smem_bytes, set_smem)) return e;
   prof_begin(s);
   core_tridiag_kernel<kCls><<<n_items, kClass[kCls].warps * 32, smem_bytes, s>>>(
       d_desc, smem_bytes, n_max, d_status);

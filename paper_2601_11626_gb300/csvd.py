@@ -74,6 +74,11 @@ def _sig(lib):
     lib.csvd_tail_error.argtypes = [VP, P(D), P(D), P(D), P(D)]
     lib.csvd_incr_free.argtypes = [VP]
     lib.csvd_score.argtypes = [P(VP), I32, P(I32), P(Block), I32, D, I32, VP, I64, VP, VP, VP]
+    lib.csvd_score_plan.argtypes = [P(VP), I32, P(I32), P(Block), I32, D, I32, VP, I64, VP, VP, VP,
+                                    P(VP)]
+    lib.csvd_plan_launch.argtypes = [VP, VP]
+    lib.csvd_plan_status.argtypes = [VP, VP]
+    lib.csvd_plan_free.argtypes = [VP]
     lib.csvd_score_columns.argtypes = [P(VP), I32, P(I32), VP, I64, I32, D, VP, I64, VP, VP, VP]
     lib.csvd_stream_init.argtypes = [P(VP), I64, I32, D, I32, VP]
     lib.csvd_stream_push.argtypes = [VP, P(Block), P(I32), P(D), P(D)]
@@ -107,7 +112,8 @@ def _sig(lib):
                  "csvd_stream_cluster", "csvd_stream_free",
                  "csvd_cluster", "csvd_tail_grad", "csvd_block_energy", "csvd_set_allocator",
                  "csvd_debug_limits", "csvd_tune_set", "csvd_tune_get", "csvd_tail_energy",
-                 "csvd_top_basis", "csvd_randomized_tail"):
+                 "csvd_top_basis", "csvd_randomized_tail", "csvd_score_plan", "csvd_plan_launch",
+                 "csvd_plan_status", "csvd_plan_free"):
         getattr(lib, name).restype = C.c_int
 
 
@@ -324,7 +330,13 @@ class Stream:
 
 class ScoreBatch:
     """Prepared descriptor arrays for repeated ``csvd_score`` calls on the
-    same candidates (avoids rebuilding ctypes arrays inside timed loops)."""
+    same candidates (avoids rebuilding ctypes arrays inside timed loops).
+
+    ``plan()`` goes further (``csvd_score_plan``): the library builds and
+    uploads everything once, ``launch()`` then only enqueues the kernels and
+    ``check()`` reads the device status; ``graph()`` captures one launch into
+    a CUDA graph.  While a plan exists the states must not be appended to and
+    the candidate tensors must stay alive (their contents may change)."""
 
     def __init__(self, states, cand_state, cands, eps, precision="mixed", r_max=None):
         self._lib = lib()
@@ -341,6 +353,7 @@ class ScoreBatch:
         self.tail = torch.zeros(self.n, device="cuda", dtype=torch.float64)
         self.paper = torch.zeros(self.n, device="cuda", dtype=torch.float64)
         self.accept = torch.zeros(self.n, device="cuda", dtype=torch.uint8)
+        self._plan = None
 
     def run(self):
         _check(self._lib.csvd_score(self._st, len(self.states), self._cs, self._cb, self.n,
@@ -350,6 +363,53 @@ class ScoreBatch:
                                     C.c_void_p(self.paper.data_ptr()),
                                     C.c_void_p(self.accept.data_ptr())))
         return self
+
+    def plan(self):
+        if self._plan is None:
+            h = C.c_void_p()
+            _check(self._lib.csvd_score_plan(self._st, len(self.states), self._cs, self._cb,
+                                             self.n, self.eps, self.precision,
+                                             C.c_void_p(self.sigma.data_ptr()), self.r_max,
+                                             C.c_void_p(self.tail.data_ptr()),
+                                             C.c_void_p(self.paper.data_ptr()),
+                                             C.c_void_p(self.accept.data_ptr()), C.byref(h)))
+            self._plan = h
+        return self
+
+    def launch(self, stream=None):
+        """Enqueue one evaluation of the plan (on ``stream``, else the
+        states' stream); no host work, no synchronisation."""
+        _check(self._lib.csvd_plan_launch(self.plan()._plan, _stream(stream) if stream else None))
+        return self
+
+    def check(self, stream=None):
+        """Synchronise and raise for device-side failures since the last check."""
+        if self._plan is not None:
+            _check(self._lib.csvd_plan_status(self._plan, _stream(stream) if stream else None))
+        return self
+
+    def graph(self):
+        """One plan launch captured into a ``torch.cuda.CUDAGraph`` (after an
+        eager launch that sets the kernels' limits); replaying it writes the
+        same outputs."""
+        self.launch().check()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=side):
+            self.launch(torch.cuda.current_stream())
+        return g
+
+    def close(self):
+        if self._plan is not None:
+            self._lib.csvd_plan_free(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class ScoreColumns:

@@ -53,6 +53,21 @@ def test_argument_errors_need_no_gpu(so):
     assert so.csvd_incr_init(ctypes.byref(h), 8, 16, 0, None) == 1   # r > m
     assert so.csvd_incr_init(ctypes.byref(h), 8, 2, 7, None) == 1    # bad precision
     assert so.csvd_incr_init(None, 8, 2, 0, None) == 1
+    # prepared evaluations: missing handles and arguments
+    vp = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    so.csvd_score_plan.argtypes = [vp, i32, vp, vp, i32, dbl, i32, vp, i64, vp, vp, vp,
+                                   ctypes.POINTER(vp)]
+    so.csvd_plan_launch.argtypes = [vp, vp]
+    so.csvd_plan_status.argtypes = [vp, vp]
+    so.csvd_plan_free.argtypes = [vp]
+    assert so.csvd_plan_launch(None, None) == 1
+    assert so.csvd_plan_status(None, None) == 1
+    assert so.csvd_plan_free(None) == 1
+    out = ctypes.c_void_p(1)
+    assert so.csvd_score_plan(None, 1, None, None, 1, 0.1, 1, None, 4, None, None, None,
+                              ctypes.byref(out)) == 1
+    assert out.value is None  # cleared on failure
 
 
 def test_binding_fails_loudly_without_gpu():

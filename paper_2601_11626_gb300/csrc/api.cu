@@ -487,6 +487,15 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
                                      cudaStream_t s, int* d_status, Workspace& ws,
                                      CommitKeep* keep, bool want_W, LaunchPlan* plan = nullptr);
 
+// Set while a caller scores candidates only for their accept decisions (the
+// clustering scan): the mixed core then re-solves in FP64 only the items
+// near the threshold (kDecisionBand) instead of every small tail.
+static thread_local bool t_decision_only = false;
+struct DecisionOnly {
+  DecisionOnly() { t_decision_only = true; }
+  ~DecisionOnly() { t_decision_only = false; }
+};
+
 // With a plan, the stream work is kept in it (and the buffers it uses move
 // into it) instead of running.
 static csvd_status run_items(const std::vector<Item>& items, double eps, int precision,
@@ -674,6 +683,7 @@ static csvd_status run_items_general(const std::vector<Item>& items, double eps,
       c.kp = o.kp;
       c.r_new = o.r_new;
       c.in_smem = o.smem ? 1 : 0;
+      c.refine_near = t_decision_only ? 1 : 0;
       c.work = o.smem ? nullptr : reinterpret_cast<float*>(base + o.work);
       c.ldwork = o.ldwork;
       if (mixed) {
@@ -1825,6 +1835,7 @@ csvd_status score_state(Driver& D, csvd_state st, const std::vector<int>& cand,
                     w.at<double>(o_t) + i, nullptr, w.at<double>(o_e) + i, nullptr};
   {
     Workspace ws;
+    DecisionOnly only_decisions;  // first_accept reads nothing but tail <= eps^2 energy
     CSVD_TRY(run_items(items, D.eps, D.precision, D.s, D.d_status, ws, nullptr, false));
   }
   CUDA_TRY(cudaMemcpyAsync(tail.data(), w.base + o_t, sizeof(double) * n, cudaMemcpyDeviceToHost, D.s));

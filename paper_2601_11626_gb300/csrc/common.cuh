@@ -94,7 +94,8 @@ struct CoreDesc {
   uint8_t* refine;       // mixed: set to 1 when the tail needs the FP64 re-solve (may be null)
   double eps;
   int rt, k, kp, r_new;  // r_new = min(r, rt + kp)
-  int in_smem, pad;
+  int in_smem;
+  int refine_near;       // mark only tails within kDecisionBand of the accept threshold
 };
 
 // ----------------------------------------------------- one-column merges
@@ -257,6 +258,11 @@ cudaError_t tc_set_wait_ns(long long ns, int stall);
 // The mixed core marks an item for the FP64 re-solve when its estimated tail
 // lies below this fraction of the merged energy.
 constexpr double kRefineFrac = 2e-3;
+// Callers that use only the accept decision (the clustering scan) re-solve
+// only the items whose FP32 tail lies within this fraction of the merged
+// energy from eps^2 times it: far above the FP32 core's error (a few u of
+// the energy), so every other decision is already exact.
+constexpr double kDecisionBand = 1e-5;
 // FP64 re-solve of the marked items of up to three core arrays: `slots`
 // persistent CTAs, each with n_max^2 doubles of `work`; *d_counter must be 0.
 size_t refine64_smem_bytes(int n_max);

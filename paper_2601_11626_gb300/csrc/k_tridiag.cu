@@ -766,7 +766,12 @@ core_tridiag_kernel(const CoreDesc* __restrict__ descs, int smem_bytes, int n_ma
       if (d.tail_paper_out) d.tail_paper_out[0] = paper;
       if (d.energy_out) d.energy_out[0] = energy_new;
       if (d.accept_out) d.accept_out[0] = (tail <= d.eps * d.eps * energy_new) ? 1 : 0;
-      if (d.refine) d.refine[0] = (tail < kRefineFrac * energy_new) ? 1 : 0;
+      if (d.refine) {
+        const bool mark = d.refine_near
+                              ? fabs(tail - d.eps * d.eps * energy_new) <= kDecisionBand * energy_new
+                              : tail < kRefineFrac * energy_new;
+        d.refine[0] = mark ? 1 : 0;
+      }
     }
   }
 }

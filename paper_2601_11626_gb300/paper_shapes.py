@@ -47,10 +47,23 @@ def make(name, scale=1.0, seed=0, device="cuda"):
     return blocks, pool
 
 
+def make_config5(scale=1.0, seed=0, device="cuda"):
+    """The differentiation + clustering collection (synth.grad_c5): 1024
+    blocks of 2048 x 256 from 32 latent subspaces of dimension 48 with a
+    spectral gap at r = 128, eps = 0.05; ``scale`` shrinks the block count."""
+    n = max(8, int(round(1024 * scale)))
+    w = synth.grad_c5(seed=seed, device=device, n_blocks=n)
+    return w["blocks"], dict(K=n, m=w["m"], k=256, r=w["r"], eps=w["eps"]), w["latent"]
+
+
 def run(name, algo="approx", sort_mode="frobenius", scale=1.0, precision="mixed", seed=0,
         decompose=True):
-    p = SHAPES[name]
-    blocks, pool = make(name, scale, seed)
+    latent = None
+    if name == "config5":
+        blocks, p, latent = make_config5(scale, seed)
+    else:
+        p = SHAPES[name]
+        blocks, pool = make(name, scale, seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = csvd.cluster(blocks, p["r"], p["eps"], algo, sort_mode, precision)
@@ -59,6 +72,14 @@ def run(name, algo="approx", sort_mode="frobenius", scale=1.0, precision="mixed"
     out = dict(shape=name, blocks=len(blocks), m=p["m"], k=p["k"], r=p["r"], eps=p["eps"],
                algo=algo, sort=sort_mode, precision=precision, cluster_seconds=wall,
                clusters=res["n_clusters"], compression_ratio=res["compression_ratio"])
+    if latent is not None:
+        # how many latent subspaces each cluster mixes (their blocks' primary ones)
+        mix = {}
+        for lab, c in zip(res["labels"], latent):
+            mix.setdefault(lab, set()).add(c)
+        out.update(max_subspaces_per_cluster=max(len(v) for v in mix.values()),
+                   clusters_per_subspace=max(sum(1 for v in mix.values() if c in v)
+                                             for c in set(latent)))
     if decompose:
         # the final decomposition uses the cluster's rank-r truncated SVD:
         # the incremental estimator at a working rank r + 16, refined by two
@@ -85,7 +106,7 @@ def _main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description="clustering on paper-shaped stand-ins")
-    ap.add_argument("--shape", choices=sorted(SHAPES), default="qualcomm")
+    ap.add_argument("--shape", choices=sorted(SHAPES) + ["config5"], default="qualcomm")
     ap.add_argument("--algo", choices=("weyl", "residual", "approx"), default="approx")
     ap.add_argument("--sort", choices=("frobenius", "residual"), default="frobenius")
     ap.add_argument("--scale", type=float, default=1.0)

@@ -182,24 +182,6 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // tcgen05.ld of 32 columns without the wait (pair with tmem_wait_ld).
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -322,11 +304,15 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
   const uint32_t b0 = smem_u32(bars);
   auto full_st = [&](int s) { return b0 + 8u * s; };
   auto empty_st = [&](int s) { return b0 + 8u * (F + s); };
-  auto full_op = [&](int s) { return b0 + 8u * (2 * F + s); };
-  auto empty_op = [&](int s) { return b0 + 8u * (2 * F + B + s); };
+  // Operand slot s and stage accumulator s are used by the same stages
+  // (B == X): ready(s) completes when the split warps have filled the slot
+  // and the epilogue has drained the accumulator two stages back, so the MMA
+  // thread waits once per stage; done(s) is the stage's single MMA commit,
+  // which frees the slot and hands the accumulator to the epilogue.
   constexpr int X = kTcXBuf;
-  auto x_full = [&](int a) { return b0 + 8u * (2 * F + 2 * B + a); };
-  auto x_empty = [&](int a) { return b0 + 8u * (2 * F + 2 * B + X + a); };
+  static_assert(X == B, "one barrier pair per operand slot and accumulator");
+  auto ready = [&](int s) { return b0 + 8u * (2 * F + s); };
+  auto done = [&](int s) { return b0 + 8u * (2 * F + B + s); };
   const uint32_t final_bar = b0 + 8u * (2 * F + 2 * B + 2 * X);
   const uint32_t stall_bar = b0 + 8u * (2 * F + 2 * B + 2 * X + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F + 2 * B + 2 * X + 2);
@@ -339,12 +325,8 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       mbar_init(empty_st(s), kTcConvWarps);
     }
     for (int s = 0; s < B; ++s) {
-      mbar_init(full_op(s), kTcConvWarps);
-      mbar_init(empty_op(s), 1);
-    }
-    for (int a = 0; a < X; ++a) {
-      mbar_init(x_full(a), 1);
-      mbar_init(x_empty(a), kTcEpiWarps);
+      mbar_init(ready(s), kTcConvWarps + kTcEpiWarps);
+      mbar_init(done(s), 1);
     }
     mbar_init(final_bar, 1);
     mbar_init(stall_bar, 1);
@@ -413,20 +395,21 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int slot = it % B;
           const uint32_t xb = it % X;
-          if (!mbar_wait(x_empty(xb), ((it / X) & 1u) ^ 1u, abort_flag) ||
-              !mbar_wait(full_op(slot), (it / B) & 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(ready(slot), (it / B) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dt = tmem_base + kXCol0 + xb * (uint32_t)kTcBN;
           const uint32_t op = smem_u32(smem + kOpBase + slot * kTcStageB);
           const uint32_t a0 = op + kOpA, b0p = ti.diag ? a0 : op + kOpB;
+          // the descriptors of a stage differ only in their start address
+          // field: add the part and row-group offsets (in 16-byte units)
+          constexpr uint64_t kPartD = kTcPartBytes >> 4, kRowsD = 2048 >> 4;
+          const uint64_t da = mn_sw128_desc(a0), db = mn_sw128_desc(b0p);
           uint32_t accf = 0u;
 #pragma unroll
           for (int s16 = 0; s16 < kTcBK / 16; ++s16) {
-            const uint32_t o = s16 * 2048;  // rows 16 s16 .. 16 s16 + 15 of each atom
-            const uint64_t ah = mn_sw128_desc(a0 + o), am = mn_sw128_desc(a0 + kTcPartBytes + o),
-                           al = mn_sw128_desc(a0 + 2 * kTcPartBytes + o);
-            const uint64_t bh = mn_sw128_desc(b0p + o), bm = mn_sw128_desc(b0p + kTcPartBytes + o),
-                           bl = mn_sw128_desc(b0p + 2 * kTcPartBytes + o);
+            // rows 16 s16 .. 16 s16 + 15 of each atom
+            const uint64_t ah = da + s16 * kRowsD, am = ah + kPartD, al = ah + 2 * kPartD;
+            const uint64_t bh = db + s16 * kRowsD, bm = bh + kPartD, bl = bh + 2 * kPartD;
             umma(dt, am, bm, idesc, accf);
             accf = 1u;
             umma(dt, al, bh, idesc, 1u);
@@ -435,12 +418,9 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
             umma(dt, ah, bm, idesc, 1u);
           }
 #pragma unroll
-          for (int s16 = 0; s16 < kTcBK / 16; ++s16) {
-            const uint32_t o = s16 * 2048;
-            umma(dt, mn_sw128_desc(a0 + o), mn_sw128_desc(b0p + o), idesc, 1u);
-          }
-          umma_commit(empty_op(slot));
-          umma_commit(x_full(xb));
+          for (int s16 = 0; s16 < kTcBK / 16; ++s16)
+            umma(dt, da + s16 * kRowsD, db + s16 * kRowsD, idesc, 1u);
+          umma_commit(done(slot));
         }
       }
       // all issued MMAs complete before TMEM is released
@@ -477,7 +457,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int fs = it % F, bs = it % B;
         if (!warp_wait(full_st(fs), (it / F) & 1u, abort_flag)) { ok = false; break; }
-        if (!warp_wait(empty_op(bs), ((it / B) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        if (!warp_wait(done(bs), ((it / B) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         const uint8_t* st = smem + fs * kTcStageF;
         uint8_t* op = smem + kOpBase + bs * kTcStageB;
 #pragma unroll
@@ -512,7 +492,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(full_op(bs));
+          mbar_arrive(ready(bs));
           mbar_arrive(empty_st(fs));
         }
       }
@@ -540,6 +520,9 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
     const int half = (warp - 2 - kTcConvWarps) >> 2;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int r = q * 32 + lane;
+    // both accumulators start empty: the first stage of each slot needs no drain
+    if (lane == 0)
+      for (int a = 0; a < X; ++a) mbar_arrive(ready(a));
     uint32_t it = 0;
     bool ok = true;
     for (int tt = blockIdx.x; ok && tt < n_tiles; tt += gridDim.x) {
@@ -548,7 +531,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
       const bool vec = (ti.ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(ti.out) & 15) == 0;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const uint32_t xb = it % X;
-        if (!warp_wait(x_full(xb), (it / X) & 1u, abort_flag)) { ok = false; break; }
+        if (!warp_wait(done(xb), (it / X) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const bool last = kb + 1 == nkb;
         bool stored = false;
@@ -592,7 +575,7 @@ tc_gram_kernel(const TcItem* __restrict__ items, const TcTile* __restrict__ tile
         if (stored) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(x_empty(xb));
+        if (lane == 0) mbar_arrive(ready(xb));  // counts toward stage it + X
       }
     }
   }

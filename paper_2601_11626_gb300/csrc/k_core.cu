@@ -203,8 +203,14 @@ __device__ void core_epilogue(const CoreDesc& d, const float* vals, int nv, bool
 
 // --------------------------------------------------------- Jacobi core
 __device__ __forceinline__ void rr_pair(int t, int p, int n, int& a, int& b) {
+  // t, p < n - 1: one conditional wrap each instead of a division
   if (p == 0) { a = n - 1; b = t; }
-  else { a = (t + p) % (n - 1); b = (t - p + (n - 1)) % (n - 1); }
+  else {
+    a = t + p;
+    if (a >= n - 1) a -= n - 1;
+    b = t - p;
+    if (b < 0) b += n - 1;
+  }
 }
 
 __global__ void __launch_bounds__(1024)

@@ -127,7 +127,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
   return false;
 }
 
-// Warp-uniform wait: lane 0 polls, the verdict is broadcast.
+// Warp-uniform wait: lane 0 polls, the result is broadcast.
 __device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
   bool ok = false;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait(a, parity, abort_flag);

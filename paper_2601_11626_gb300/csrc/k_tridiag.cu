@@ -378,12 +378,14 @@ __device__ __forceinline__ void mem_tiles(float* base, int Lbase, int La, int Lb
 
 // TMEM tiles go to lane quarters in pairs: tile t sits in quarter
 // (t / 2) % 4 at slot 2 (t / 8) + t % 2.  Index j of quarter q's tiles:
-__device__ __forceinline__ int tm_tile(int q, int j) { return 8 * (j >> 1) + 2 * q + (j & 1); }
+__host__ __device__ __forceinline__ int tm_tile(int q, int j) { return 8 * (j >> 1) + 2 * q + (j & 1); }
 // number of quarter-q tiles below position t
-__device__ __forceinline__ int tm_count(int q, int t) {
+__host__ __device__ __forceinline__ int tm_count(int q, int t) {
   return 2 * (t >> 3) + min(max(t - 8 * (t >> 3) - 2 * q, 0), 2);
 }
-__device__ __forceinline__ uint32_t tm_slot(int t) { return (uint32_t)(((t >> 3) << 1) | (t & 1)); }
+__host__ __device__ __forceinline__ uint32_t tm_slot(int t) {
+  return (uint32_t)(((t >> 3) << 1) | (t & 1));
+}
 
 // The warp's TMEM tiles: quarter q's tiles j in [ja, jb), at positions Lt + t.
 __device__ __forceinline__ void tmem_tiles(uint32_t tq, int q, int ja, int jb, int a, int b,
@@ -882,6 +884,34 @@ std::string tridiag_selftest() {
       if (!ok || !col_boundary) {
         snprintf(buf, sizeof buf, "tile layout n = %d, class %d, n_max %d: T %d Lg %d Lt %d Ntm %d",
                  n, cls, n_max, L.T, L.Lg, L.Lt, L.Ntm);
+        return buf;
+      }
+    }
+  }
+  // TMEM tile placement: every tile of [0, Ntm) in exactly one lane quarter,
+  // at a slot of that quarter below its capacity, indices consistent both ways
+  for (int cls = 0; cls < 3; ++cls) {
+    const int slots = kTmemColsOf[cls] / 32;
+    for (int ntm = 0; ntm <= 4 * slots; ++ntm) {
+      int total = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int cnt = tm_count(q, ntm);
+        total += cnt;
+        unsigned used = 0;
+        for (int j = 0; j < cnt; ++j) {
+          const int t = tm_tile(q, j);
+          const uint32_t sl = tm_slot(t);
+          if (t < 0 || t >= ntm || ((t >> 1) & 3) != q || tm_count(q, t) != j ||
+              sl >= (uint32_t)slots || ((used >> sl) & 1u)) {
+            snprintf(buf, sizeof buf, "TMEM placement class %d, %d tiles, quarter %d, index %d",
+                     cls, ntm, q, j);
+            return buf;
+          }
+          used |= 1u << sl;
+        }
+      }
+      if (total != ntm) {
+        snprintf(buf, sizeof buf, "TMEM placement class %d covers %d of %d tiles", cls, total, ntm);
         return buf;
       }
     }

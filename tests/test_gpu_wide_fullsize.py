@@ -1,9 +1,10 @@
 """The wide regime at full size (weight-matrix-shaped config): two 4096 x
-4096 bf16 matrices W_i = B C_i + E_i at r = 256.  The state of the first is
-built by the FP64 oracle (one exact rank-256 truncation) and loaded; the
-second is scored in the mixed form from bf16 storage, a merge whose core has
-n = r + k = 4352 (Lemma 1 / Cor. 3 with k' = m - r_t = 3840 new directions),
-and compared with the oracle's evaluation of the same merge."""
+4096 bf16 matrices W_i = B C_i + E_i at r = 256 and r = 512.  The state of
+the first is built by the FP64 oracle (one exact rank-r truncation) and
+loaded; the second is scored in the mixed form from bf16 storage, a merge
+whose core has n = r + k = 4352 or 4608 (Lemma 1 / Cor. 3 with
+k' = m - r_t new directions), and compared with the oracle's evaluation of
+the same merge."""
 import math
 import time
 
@@ -17,10 +18,11 @@ from paper_2601_11626_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_wide_regime_full_size_one_merge(cuda_lib):
+@pytest.mark.parametrize("r", [256, 512])
+def test_wide_regime_full_size_one_merge(cuda_lib, r):
     from paper_2601_11626_gb300 import csvd
     w = synth.weights_c3(n_mats=2, device="cuda")
-    m, r = w["m"], 256
+    m = w["m"]
     a0, a1 = (b.cpu() for b in w["blocks"])
     ost = oinc.IncrementalSVD(m, r)
     ost.append(a0.float())

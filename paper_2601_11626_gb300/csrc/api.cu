@@ -1712,13 +1712,6 @@ static csvd_status span_extend(SpanState& sp, const csvd_block& R, const std::ve
   return st;
 }
 
-static double top_r_sum_sq(std::vector<double> v, int r) {
-  std::sort(v.begin(), v.end(), std::greater<double>());
-  double t = 0.0;
-  for (int i = 0; i < r && i < (int)v.size(); ++i) t += v[i] * v[i];
-  return t;
-}
-
 // sum of mu^2 beyond the r largest: with the projection energies this gives
 // Cor. 1's bound  S - sum_{j<=r} mu_j^2 = sum_i ||Q_{i-1}^T A_i||^2 +
 // sum_{j>r} mu_j^2  (since ||A_i||^2 = ||Q^T A_i||^2 + ||R_i||^2 and

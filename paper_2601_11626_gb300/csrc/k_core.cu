@@ -19,7 +19,6 @@ namespace csvd {
 
 constexpr int kJacobiMaxSweeps = 40;
 __device__ int d_jacobi_cap = kJacobiMaxSweeps;  // lowered only by the failure-path test hook
-constexpr int kBisectMaxIter = 64;
 
 // ------------------------------------------------------------- energy
 __global__ void __launch_bounds__(256)

@@ -263,10 +263,6 @@ __device__ __forceinline__ void load_group<2, TmemTile>(const TmemTile (&tl)[2],
   }
 }
 
-__device__ __forceinline__ float smem_tile_elem(const float* tp, int i, int j) {
-  return tp[i * kTile + (((j >> 2) ^ (i & 7)) << 2) + (j & 3)];
-}
-
 // K tiles of one tile column b (rows a, a + 1, ...), 16 columns at a time:
 // G -= vp wp^T + wp vp^T, row sums (two partial chains per tile, added to
 // p[row]) and column sums (kept in cp across the tiles of the column),

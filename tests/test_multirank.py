@@ -1,10 +1,11 @@
-"""The multi-rank bench path on CPU: two gloo ranks.
+"""The multi-rank paths on CPU, as gloo ranks on 127.0.0.1.
 
 Batched scoring shards by candidates with no exchange on the data path;
 each rank generates its own workload from its rank seed, and the job's
 throughput is every rank's units over the slowest rank's time (one MAX
-all-reduce of the timing).  This checks that aggregation and that the
-rank-seeded workloads differ, with two processes on 127.0.0.1.
+all-reduce of the timing).  The sharded Alg. 3 scan deals each chunk of
+candidates to the ranks and must reproduce the single-process clustering
+with two or three ranks, and a failing rank must make the others fail fast.
 """
 import os
 import socket
@@ -125,24 +126,24 @@ def _sharded_worker(rank, world, port, out, chunk):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("chunk", [3, 64])
-def test_sharded_alg3_scan_equals_single_rank(chunk):
-    """Two gloo ranks run Alg. 3 (frobenius scan) on the small recipe with the
-    candidate queue dealt to the ranks by position, and the cluster state
-    broadcast after each commit: labels, members in joining order and the
-    per-cluster estimates equal the single-process oracle clustering, every
-    rank returns the same result, and both ranks do scoring work.  A chunk
-    of 3 puts accepts in the middle of chunks (stale scores discarded)."""
+@pytest.mark.parametrize("world,chunk", [(2, 3), (2, 64), (3, 3)])
+def test_sharded_alg3_scan_equals_single_rank(world, chunk):
+    """Two or three gloo ranks run Alg. 3 (frobenius scan) on the small recipe
+    with the candidate queue dealt to the ranks by position, and the cluster
+    state broadcast after each commit: labels, members in joining order and
+    the per-cluster estimates equal the single-process oracle clustering,
+    every rank returns the same result, and every rank does scoring work.  A
+    chunk of 3 puts accepts in the middle of chunks (stale scores
+    discarded)."""
     from oracle import cluster as ocluster
     from paper_2601_11626_gb300 import synth
     col = synth.small_c1()
     want = ocluster.cluster(col.blocks, col.meta["r"], col.meta["eps"], "approx", "frobenius")
-    world = 2
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_sharded_worker, args=(world, _free_port(), out, chunk), nprocs=world,
                        join=True, start_method="spawn")
-    assert set(out.keys()) == {0, 1}
+    assert set(out.keys()) == set(range(world))
     for rank in range(world):
         labels, clusters, est, scored = out[rank]
         assert labels == want["labels"]
@@ -151,3 +152,50 @@ def test_sharded_alg3_scan_equals_single_rank(chunk):
             assert a == pytest.approx(b, rel=1e-9, abs=1e-12)
         assert len(scored) > 0
     assert len(want["clusters"]) > 1 and max(len(c) for c in want["clusters"]) > 1
+
+
+def _failing_worker(rank, world, port, out):
+    """Rank 1's scoring raises on its first call; every rank records how it
+    ended instead of exiting with the exception."""
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    try:
+        from paper_2601_11626_gb300 import sharded, synth
+        col = synth.small_c1()
+        be = _OracleBackend(col.blocks, col.meta["r"], col.meta["eps"])
+        if rank == 1:
+            def broken(st, idx):
+                raise RuntimeError("planted scoring failure")
+            be.score = broken
+        sharded.cluster_approx_sharded(be, len(col.blocks), col.meta["eps"], chunk=4)
+        out[rank] = ("finished", "")
+    except Exception as e:  # noqa: BLE001 -- the test inspects how each rank ended
+        out[rank] = ("error", f"{type(e).__name__}: {e}"[:300])
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_scan_fails_fast_when_a_rank_fails():
+    """A rank whose scoring raises leaves the scan between collectives; the
+    other rank's next collective ends with an error (the peer closed its
+    connection, or the 20 s process-group timeout) instead of waiting for
+    ever, and neither rank reports a result."""
+    import time
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    ctx = mp.start_processes(_failing_worker, args=(world, _free_port(), out), nprocs=world,
+                             join=False, start_method="spawn")
+    t0 = time.time()
+    for p in ctx.processes:
+        p.join(timeout=90)
+    alive = [p for p in ctx.processes if p.is_alive()]
+    for p in alive:
+        p.terminate()
+    assert not alive, "a rank hung after its peer failed"
+    assert time.time() - t0 < 90
+    assert out[1][0] == "error" and "planted scoring failure" in out[1][1]
+    assert out[0][0] == "error", out[0]

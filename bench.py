@@ -481,11 +481,12 @@ def run_k1(args, world, rank, local):
     work = [_k1_work(m, ranks[cs[j]], min(r, ranks[cs[j]] + 1)) for j in range(n)]
     flops = sum(x["flops"] for x in work)
     nl, tms = prof.get("core_arrow", (0, float("nan")))
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops * args.steps / (tms / 1000.0) / 1e12
     roof = {"kernel": "core_arrow", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-            "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock",
+            "peak_note": f"FP32 SIMT: {n_sm} SMs x 128 lanes x 2 flop x max SM clock",
             "hbm_gbs": sum(x["bytes"] for x in work) * args.steps / (tms / 1000.0) / 1e9,
             "kernels": {k: {"launches": v[0], "ms": v[1],
                             "share": v[1] / sum(x[1] for x in prof.values())}
@@ -761,12 +762,13 @@ def main():
         g[0] += nl_k
         g[1] += ms_k
     name, (nl, tms) = max(groups.items(), key=lambda kv: kv[1][1])
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if name.startswith("core"):
         achieved = core_flops * args.steps / (tms / 1000.0) / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+                "peak_note": f"FP32 SIMT: {n_sm} SMs x 128 lanes x 2 flop x max SM clock"}
     else:
         achieved = gram_bytes * args.steps / (tms / 1000.0) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],

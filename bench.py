@@ -449,13 +449,6 @@ def run_k1(args, world, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # launch-class edges of the eigen core for this batch (untimed)
-    tuning = None
-    if args.tune and args.precision != "plain":
-        from paper_2601_11626_gb300 import tune
-        tuning = tune.autotune(batch, [ranks[w["cand_state"][i]] + cands[i].shape[1]
-                                       for i in range(n)], m, ranks, steps=2)
-        tuning["edges"] = list(tuning["edges"])
     for _ in range(args.warmup):
         batch.run()
     barrier()

@@ -124,6 +124,44 @@ def test_exhaustive_tiny():
     assert math.isclose(out["compression_ratio"], best)
 
 
+def test_exhaustive_eight_blocks():
+    """All 4140 partitions (Bell(8)) of 8 blocks drawn from three latent
+    2-dim subspaces of R^8 (r = 2): the greedy outputs are feasible, none
+    stores fewer numbers than the best feasible partition, and Alg. 3 with
+    the norm order reaches that optimum (one cluster per latent subspace)."""
+    rng = np.random.default_rng(8)
+    Q = _orth(rng, 8, 6)
+    groups = [0, 1, 2, 0, 1, 2, 0, 1]
+    blocks = [Q[:, 2 * g:2 * g + 2] @ rng.standard_normal((2, 2)) * rng.uniform(0.5, 2)
+              + 1e-4 * rng.standard_normal((8, 2)) for g in groups]
+    r, eps, m = 2, 0.05, 8
+    widths = [2] * 8
+    feasible = {}
+
+    def ok(c):
+        key = frozenset(c)
+        if key not in feasible:
+            feasible[key] = exact.rel_error([blocks[j] for j in c], r) <= eps
+        return feasible[key]
+
+    best, n_parts = None, 0
+    for p in _partitions(list(range(8))):
+        n_parts += 1
+        if all(ok(c) for c in p):
+            cr = cluster.compression_ratio(p, widths, m, r)
+            best = cr if best is None else max(best, cr)
+    assert n_parts == 4140
+    for algo, mode in [("weyl", "frobenius"), ("residual", "frobenius"), ("approx", "frobenius"),
+                       ("approx", "residual")]:
+        out = cluster.cluster(blocks, r, eps, algo, mode)
+        for c in out["clusters"]:
+            assert exact.rel_error([blocks[j] for j in c], r) <= eps * (1 + 1e-9)
+        assert out["compression_ratio"] <= best + 1e-12
+    out = cluster.cluster(blocks, r, eps, "approx", "frobenius")
+    assert math.isclose(out["compression_ratio"], best)
+    assert sorted(sorted(c) for c in out["clusters"]) == [[0, 3, 6], [1, 4, 7], [2, 5]]
+
+
 def test_compression_ratio_closed_form():
     """Section 4: K blocks of m x n at rank r store r (m + K n) numbers;
     clusters that would not shrink are stored raw."""

@@ -248,6 +248,35 @@ def test_bounds_are_upper_bounds_random():
         assert w >= ex - eps and res >= ex - eps and plug >= ex - eps
 
 
+def test_bounds_are_upper_bounds_ten_thousand_tiny():
+    """10^4 tiny collections (m <= 6, up to four blocks of up to three
+    columns), a quarter of them degenerate: a block repeated (nested
+    ranges), a block scaled from another, a zero block, or blocks of rank
+    one.  The Weyl, residual and plug-in values never fall below the exact
+    Eckart-Young tail, and the energies agree."""
+    rng = np.random.default_rng(2026)
+    for i in range(10_000):
+        m = int(rng.integers(2, 7))
+        blocks = [rng.standard_normal((m, int(rng.integers(1, 4)))) * rng.uniform(0.1, 2)
+                  for _ in range(int(rng.integers(1, 5)))]
+        kind = i % 8
+        if kind == 1 and len(blocks) > 1:
+            blocks[-1] = blocks[0].copy()
+        elif kind == 3 and len(blocks) > 1:
+            blocks[-1] = blocks[0] * rng.uniform(-3, 3)
+        elif kind == 5:
+            blocks[int(rng.integers(len(blocks)))] = np.zeros((m, 2))
+        elif kind == 7:
+            blocks = [np.outer(rng.standard_normal(m), rng.standard_normal(b.shape[1]))
+                      for b in blocks]
+        r = int(rng.integers(1, m + 1))
+        ex = exact.tail_sq(blocks, r)
+        w, res, plug, en = bounds.all_bounds(blocks, r)
+        assert math.isclose(en, exact.energy(blocks), rel_tol=1e-12, abs_tol=1e-300)
+        tol = 1e-10 * max(en, 1e-300)
+        assert w >= ex - tol and res >= ex - tol and plug >= ex - tol, (i, w, res, plug, ex)
+
+
 def test_weyl_rank_one_example():
     """Appendix D, Example 1: shared left vector -> E_1 = 0 but the Weyl
     bound equals sum s_j^2 - max s_j^2."""
